@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the trident SpGEMM hot path on GB300.
+
+Default workload (N=1): C = A B with A, B independent Erdos-Renyi CSR
+matrices, n = 2^20, 16 nonzeros per row at distinct uniform columns, float64
+values U(-1, 1), seeds 0 / 1 (268,435,456 intermediate products).  One step =
+the whole product: analysis + symbolic + scan (+ nnz read back) + numeric.
+Metric: SpGEMM GFLOP/s = 2 x intermediate products / second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload
+(independent problems, no collective on the data path); the time is the max
+over ranks and the value counts all ranks' products.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpGEMM GFLOP/s (2x intermediate products/s)"
+UNIT = "GFLOP/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--n-log2", type=int, default=20)
+    p.add_argument("--d", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    import gen
+    n = 1 << args.n_log2
+    A = gen.er(n, n, args.d, 0, np.float64)
+    B = gen.er(n, n, args.d, 1, np.float64)
+    return n, A, B
+
+
+def products(A, B) -> int:
+    return int(np.diff(B.rowptr)[A.col].sum())
+
+
+def algorithmic_bytes(A, B, nnz_c: int, val_bytes: int = 8):
+    """Compulsory bytes of the numeric pass (read A and B once, read C's
+    row_ptr, write C's columns and values) and of the symbolic pass (read the
+    index arrays of A and B, write C's row_ptr)."""
+    m, k = A.nrows, B.nrows
+    numeric = (4 * (m + 1) + A.nnz * (4 + val_bytes) + 4 * (k + 1) + B.nnz * (4 + val_bytes)
+               + 4 * (m + 1) + nnz_c * (4 + val_bytes))
+    symbolic = 4 * (m + 1) + 4 * A.nnz + 4 * (k + 1) + 4 * B.nnz + 4 * (m + 1)
+    return numeric, symbolic
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(A, B, budget_rows: int):
+    """The oracle, as it stands, on the first ``budget_rows`` rows of A."""
+    import gen
+    import oracle
+    rows = min(budget_rows, A.nrows)
+    end = int(A.rowptr[rows])
+    As = gen.CSR(rows, A.ncols, A.rowptr[:rows + 1].copy(), A.col[:end], A.val[:end])
+    prods = products(As, B)
+    oracle.spgemm(As, B, with_scale=False)  # warm (first-touch, thread pool)
+    t0 = time.perf_counter()
+    oracle.spgemm(As, B, with_scale=False)
+    dt = time.perf_counter() - t0
+    return {"value": round(2 * prods / dt / 1e9, 4), "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"first {rows} of {A.nrows} rows ({prods} products), 1 timed run after 1 warm run"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n, A, B = workload(args)
+    import gen
+    import oracle
+    rows = 1 << 15
+    end = int(A.rowptr[rows])
+    As = gen.CSR(rows, A.ncols, A.rowptr[:rows + 1].copy(), A.col[:end], A.val[:end])
+    prods = products(As, B)
+    for _ in range(max(args.warmup, 0)):
+        oracle.spgemm(As, B, with_scale=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spgemm(As, B, with_scale=False)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    val = 2 * prods / dt / 1e9
+    line = {"metric": METRIC, "value": round(val, 4), "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"ER A*B n=2^{args.n_log2} d={args.d} f64 (seeds 0/1)",
+                       "global_batch": 1, "seq_len": None, "parallelism": "replicas"},
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"first {rows} of {n} rows ({prods} products) per step"},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    import paper_2603_21444_gb300 as tsg
+
+    n, A, B = workload(args)
+    prods = products(A, B)
+    dA = tsg.DeviceCSR.from_host(A)
+    dB = tsg.DeviceCSR.from_host(B)
+    h = tsg.Handle()
+    stream = torch.cuda.current_stream()
+    rp, nnz = tsg.symbolic(dA, dB, h)
+    C = tsg.DeviceCSR(n, n, rp, torch.empty(nnz, dtype=torch.int32, device="cuda"),
+                      torch.empty(nnz, dtype=torch.float64, device="cuda"))
+
+    # each step writes into the same C: symbolic into C.row_ptr, numeric into C.col / C.val
+    import ctypes
+    from paper_2603_21444_gb300 import _abi
+    a_in, b_in = dA.as_in(), dB.as_in()
+    c_out = C.as_out()
+    nnz_box = ctypes.c_int64()
+    L = _abi.lib()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def step():
+        _abi.check(L.spgemm_symbolic(h.ptr, ctypes.byref(a_in), ctypes.byref(b_in), ctypes.c_void_p(c_out.row_ptr),
+                                     ctypes.byref(nnz_box), sptr), "symbolic")
+        _abi.check(L.spgemm_numeric(h.ptr, _abi.F64, ctypes.byref(a_in), ctypes.byref(b_in), ctypes.byref(c_out),
+                                    sptr), "numeric")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    h.read_timing()
+    h.set_timing(True)
+    launches0 = h.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = h.launch_count() - launches0
+    h.set_timing(False)
+    phase_ms, phase_cnt = h.read_timing()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2 * prods / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (numeric rows): algorithmic bytes per launch / duration
+    num_bytes, sym_bytes = algorithmic_bytes(A, B, nnz)
+    peak, peak_kind = peaks()
+    num_ms = phase_ms[3] / max(phase_cnt[3], 1)
+    sym_ms = phase_ms[1] / max(phase_cnt[1], 1)
+    achieved = num_bytes / (num_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_num_rows<32,8,double> (numeric rows)", "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": peak_kind, "algorithmic_bytes": num_bytes, "launch_ms": round(num_ms, 4)}
+    phases = {"analysis_ms": phase_ms[0] / args.steps, "symbolic_rows_ms": sym_ms, "scan_ms": phase_ms[2] / args.steps,
+              "numeric_rows_ms": num_ms, "heavy_ms": phase_ms[4] / args.steps,
+              "symbolic_frac_of_hbm": round(sym_bytes / (sym_ms * 1e-3) / 1e9 / peak, 4) if sym_ms > 0 else None}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = e2e_public_api(tsg, A, B, prods, args)
+
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline and world == 1:
+            cb = cpu_baseline(A, B, 1 << 17)
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"ER A*B n=2^{args.n_log2} d={args.d} f64 (seeds 0/1), plain product",
+                           "model": None, "global_batch": world, "seq_len": None,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "products": prods, "nnz_c": nnz, "l2": "inputs+outputs > L2 (C = "
+                           f"{nnz * 12 / 1e9:.2f} GB written per step)"},
+                "roofline": roof, "phases": {k: (round(v, 4) if isinstance(v, float) else v)
+                                              for k, v in phases.items()},
+                "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_public_api(tsg, A, B, prods, args):
+    """Same metric through the public API with host inputs: pinned host A, B
+    copied in, C = A B, C copied back to pinned host memory, every step."""
+    import torch
+    hostA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+             for k, v in (("rp", A.rowptr.astype(np.int32)), ("col", A.col), ("val", A.val))}
+    hostB = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+             for k, v in (("rp", B.rowptr.astype(np.int32)), ("col", B.col), ("val", B.val))}
+    h = tsg.Handle()
+    out = {}
+
+    def step():
+        dA = tsg.DeviceCSR(A.nrows, A.ncols, hostA["rp"].to("cuda", non_blocking=True),
+                           hostA["col"].to("cuda", non_blocking=True), hostA["val"].to("cuda", non_blocking=True))
+        dB = tsg.DeviceCSR(B.nrows, B.ncols, hostB["rp"].to("cuda", non_blocking=True),
+                           hostB["col"].to("cuda", non_blocking=True), hostB["val"].to("cuda", non_blocking=True))
+        C = tsg.spgemm(dA, dB, h)
+        if "col" not in out or out["col"].numel() != C.nnz:
+            out["rp"] = torch.empty(C.nrows + 1, dtype=torch.int32).pin_memory()
+            out["col"] = torch.empty(C.nnz, dtype=torch.int32).pin_memory()
+            out["val"] = torch.empty(C.nnz, dtype=torch.float64).pin_memory()
+        out["rp"].copy_(C.row_ptr, non_blocking=True)
+        out["col"].copy_(C.col, non_blocking=True)
+        out["val"].copy_(C.val, non_blocking=True)
+        return C.nnz
+
+    nnz = step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    h2d = sum(int(v.numel() * v.element_size()) for v in list(hostA.values()) + list(hostB.values()))
+    d2h = (A.nrows + 1) * 4 + nnz * 12
+    h.close()
+    return {"value": round(2 * prods / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3), "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * trident_spgemm.h -- C ABI of the GB300 (sm_103a) trident SpGEMM library.
+ *
+ * The library computes the local hot path of the trident distributed SpGEMM
+ * (Communication-Avoiding SpGEMM via Trident Partitioning, arXiv 2603.21444):
+ * the per-block CSR product C_blk = A_blk B_blk (row-wise Gustavson: a
+ * symbolic pass that sizes every output row, then a numeric pass) and the
+ * ordered sum of the partial products that the sqrt(P/lambda) x
+ * sqrt(P/lambda) x lambda trident grid assigns to each output block
+ * (Sec. 3.2, Alg. 1, Alg. 2, Sec. 4.4).  On one GPU all blocks run as batched
+ * instances; there is no inter-GPU traffic.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Matrices are CSR (Sec. 2): row_ptr (nrows+1 int32), col_idx (nnz int32),
+ * val (nnz values, float or double as the call's spgemm_dtype says).
+ *
+ * Ownership: every array passed in or out is DEVICE memory allocated and
+ *   owned by the caller; no call frees or keeps caller memory beyond the
+ *   call.  The handle owns only its own workspace (grown on demand with
+ *   cudaMalloc, released by spgemm_destroy).  Pointers marked "host" are
+ *   ordinary host memory.
+ * Streams: all device work is ordered on the stream passed in (a
+ *   cudaStream_t; NULL means the legacy default stream).  Calls that return a
+ *   size to the host (symbolic, sizing calls) synchronise that stream once.
+ * Input canonical form: row_ptr non-decreasing with row_ptr[0] = 0 and
+ *   row_ptr[nrows] = nnz, 0 <= col_idx < ncols.  Columns need not be sorted
+ *   for the product to be correct, but output rows are always written sorted
+ *   ascending and duplicate-free, so outputs are canonical.  With
+ *   tune.validate != 0 inputs are checked on the device first and a bad one
+ *   gives SPGEMM_ERR_NOT_CANONICAL; with validation off a bad input is
+ *   undefined behaviour.
+ * Output pattern: structural; an entry exists wherever a product a_ik b_kj
+ *   lands, explicit zeros from cancellation are kept.
+ * Values: each product is rounded once and the products of an output entry
+ *   are added in ascending (instance, k) order, each instance's products
+ *   summed first (deterministic accumulator, SPGEMM_ACC_SORT); rows with more
+ *   than 8192 products use a dense accumulator with atomic adds whose order is
+ *   not fixed (results then agree to rounding, not bit for bit).
+ * Sizes: per output matrix nnz must fit int32; otherwise the sizing call
+ *   returns SPGEMM_ERR_INDEX_OVERFLOW and no numeric work may follow.
+ * Errors: returned, never thrown.  On error the content of the outputs is
+ *   unspecified.  A device-side inconsistency is latched in the handle and
+ *   reported by spgemm_device_status().
+ * Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef TRIDENT_SPGEMM_H
+#define TRIDENT_SPGEMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t without including CUDA headers; NULL = legacy default stream. */
+typedef struct CUstream_st* spgemm_stream_t;
+
+typedef enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID_ARG = 1,     /* null pointer, negative size, bad enum */
+    SPGEMM_ERR_SHAPE = 2,           /* A.ncols != B.nrows, mismatched output shape */
+    SPGEMM_ERR_DTYPE = 3,           /* unknown value type */
+    SPGEMM_ERR_INDEX_OVERFLOW = 4,  /* an output's nnz exceeds INT32_MAX */
+    SPGEMM_ERR_OOM = 5,             /* workspace allocation failed */
+    SPGEMM_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    SPGEMM_ERR_DEVICE_TIMEOUT = 7,  /* a bounded device wait ran out */
+    SPGEMM_ERR_HASH_OVERFLOW = 8,   /* an accumulator saw more entries than sized for */
+    SPGEMM_ERR_NOT_CANONICAL = 9,   /* input failed validation */
+    SPGEMM_ERR_INTERNAL = 10,       /* device consistency check failed */
+    SPGEMM_ERR_UNSUPPORTED = 11     /* valid request this build does not handle */
+} spgemm_status;
+
+typedef enum { SPGEMM_F32 = 0, SPGEMM_F64 = 1 } spgemm_dtype;
+
+/* Input CSR (device pointers).  val may be NULL for the symbolic pass. */
+typedef struct {
+    int32_t nrows;
+    int32_t ncols;
+    int32_t nnz;
+    const int32_t* row_ptr; /* nrows + 1 */
+    const int32_t* col_idx; /* nnz */
+    const void* val;        /* nnz values of the call's dtype */
+} spgemm_csr_in;
+
+/* Output CSR (device pointers, caller-allocated).  row_ptr is written by the
+ * sizing/symbolic call and read by the numeric call. */
+typedef struct {
+    int32_t nrows;
+    int32_t ncols;
+    int32_t* row_ptr; /* nrows + 1 */
+    int32_t* col_idx; /* nnz (NULL in a sizing call) */
+    void* val;        /* nnz */
+} spgemm_csr_out;
+
+/* Row bins.  Rows are binned by their intermediate-product count
+ * u_i = sum_{k in A_i} |B_k| (and their A-row length).  Bin b serves rows with
+ * u <= bin_upper[b] using kernel variant bin_kernel[b] (an index into the
+ * variant table below); rows beyond the last bin use the dense heavy-row path.
+ * Kernel variants (team = threads cooperating on one row, capacity = most
+ * products a team holds on chip):
+ *   0: warp,  32   1: warp, 64    2: warp, 128    3: warp, 256    4: warp, 512
+ *   5: 128 threads, 1024   6: 256 threads, 2048   7: 512 threads, 4096
+ *   8: 512 threads, 8192
+ * A variant whose capacity is below bin_upper is rejected. */
+#define SPGEMM_MAX_BINS 12
+#define SPGEMM_NUM_VARIANTS 9
+enum { SPGEMM_ACC_SORT = 0 };
+
+typedef struct {
+    int32_t num_bins;                      /* 1..SPGEMM_MAX_BINS */
+    int32_t bin_upper[SPGEMM_MAX_BINS];    /* increasing product-count bounds */
+    int32_t bin_kernel[SPGEMM_MAX_BINS];   /* variant per bin */
+    int32_t accumulator;                   /* SPGEMM_ACC_SORT */
+    int32_t warps_per_block;               /* blocks of warp-team variants: 1..16 */
+    int32_t validate;                      /* nonzero: check inputs on the device */
+} spgemm_tune;
+
+typedef struct spgemm_handle spgemm_handle;
+
+/* ---------------------------------------------------------------- handles */
+
+/* Static string for a status code (never NULL). */
+const char* spgemm_status_str(spgemm_status s);
+
+/* Library version string. */
+const char* spgemm_version(void);
+
+/* Create a handle bound to the CUDA device current on the calling thread.
+ * *out receives the handle; SPGEMM_ERR_CUDA if no device is usable. */
+spgemm_status spgemm_create(spgemm_handle** out);
+
+/* Free the handle's workspace and the handle (NULL is a no-op).  Waits for
+ * the handle's outstanding work on every stream it used. */
+spgemm_status spgemm_destroy(spgemm_handle* h);
+
+/* Fill *t with the library's default tuning (no handle needed). */
+spgemm_status spgemm_default_tune(spgemm_tune* t);
+
+/* Set the tuning used by later calls (NULL restores the defaults).  Checked:
+ * bounds increasing, variants known and large enough. */
+spgemm_status spgemm_set_tune(spgemm_handle* h, const spgemm_tune* t);
+spgemm_status spgemm_get_tune(const spgemm_handle* h, spgemm_tune* t);
+
+/* ------------------------------------------------------- the product (Sec. 2)
+ *
+ * spgemm_symbolic: row sizes of C = A B.  Writes c_row_ptr (device, m+1,
+ * int32) as the exclusive scan of the per-row distinct-column counts and
+ * *c_nnz (host) = nnz(C).  B.val / A.val are not read.  Synchronises the
+ * stream once (to return nnz).  SPGEMM_ERR_SHAPE if A.ncols != B.nrows,
+ * SPGEMM_ERR_INDEX_OVERFLOW if nnz(C) > INT32_MAX (c_row_ptr then unspecified).
+ */
+spgemm_status spgemm_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                              int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream);
+
+/* spgemm_numeric: fills C->col_idx and C->val (device, nnz(C) each) of
+ * C = A B, reading C->row_ptr as written by spgemm_symbolic for the same
+ * A and B patterns.  Rows are written sorted.  Asynchronous (no host sync). */
+spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
+                             const spgemm_csr_in* B, spgemm_csr_out* C, spgemm_stream_t stream);
+
+/* ------------------------------------ ordered sum of partials (Sec. 4.4, Alg. 1)
+ *
+ * spgemm_merge: C = parts[0] + parts[1] + ... + parts[nparts-1] for CSR
+ * matrices of one shape (the accumulation C_ijk += C_ijk^(r) of Alg. 1 over
+ * the rounds r, done by cuSPARSE spgeam in the paper).  Row i of C is the
+ * union of the row-i patterns; equal columns are added in part order.
+ * Sizing call: C->col_idx == NULL -> writes C->row_ptr and *c_nnz (host),
+ * synchronising once.  Fill call: C->col_idx != NULL -> fills col/val using
+ * C->row_ptr from the sizing call; c_nnz may be NULL; asynchronous.
+ * 1 <= nparts <= 64.
+ */
+spgemm_status spgemm_merge(spgemm_handle* h, spgemm_dtype dtype, int32_t nparts,
+                           const spgemm_csr_in* parts, spgemm_csr_out* C, int64_t* c_nnz,
+                           spgemm_stream_t stream);
+
+/* ------------------------------- batched instances (Alg. 1 + Alg. 2, Sec. 3.3)
+ *
+ * spgemm_batched: many products in one pass.  Instance t is A[t] B[t].
+ * Instances are grouped: group g owns instances [group_ptr[g],
+ * group_ptr[g+1]) (host array, ngroups+1 entries; NULL means one instance
+ * per group) and its output C[g] = sum over its instances, in that order, of
+ * A[t] B[t] -- the trident output block C_ijk = sum_r A_{i r' k} B_{r' j}
+ * with the rounds listed in stagger order.  All instances of a group must
+ * have the same A.nrows and B.ncols (= C[g] shape).  B[t] of different
+ * instances may alias the same device arrays (a shared tile is read in
+ * place; on one device this is the allgathered tile of Alg. 2).
+ * The partials are never materialised: each output row accumulates all its
+ * instances at once, adding each instance's products first and then the
+ * instance sums in group order (the same sums spgemm_merge of the partials
+ * would give).
+ * Sizing call: c_nnz != NULL -> writes every C[g].row_ptr and c_nnz[g]
+ * (host, ngroups entries), synchronising once; col_idx/val are not read.
+ * Fill call: c_nnz == NULL -> fills every C[g].col_idx / val (NULL allowed
+ * only for a group whose nnz is 0), asynchronous.
+ * tune: NULL uses the handle's tuning.  ninst <= 2^20, group sizes <= 64.
+ */
+spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst,
+                             const spgemm_csr_in* A, const spgemm_csr_in* B, int32_t ngroups,
+                             const int32_t* group_ptr, spgemm_csr_out* C, int64_t* c_nnz,
+                             const spgemm_tune* tune, spgemm_stream_t stream);
+
+/* --------------------------------------------------------- instrumentation */
+
+/* Number of kernels this handle has launched since creation (host counter). */
+spgemm_status spgemm_launch_count(const spgemm_handle* h, int64_t* count);
+
+/* Synchronise the handle's last stream and report a latched device-side
+ * inconsistency (SPGEMM_ERR_INTERNAL / SPGEMM_ERR_HASH_OVERFLOW /
+ * SPGEMM_ERR_DEVICE_TIMEOUT) or SPGEMM_OK; clears the latch. */
+spgemm_status spgemm_device_status(spgemm_handle* h);
+
+/* Per-phase CUDA-event timing.  enable != 0 starts recording events around
+ * each phase on the call's stream; spgemm_read_timing synchronises, adds up
+ * the completed intervals and returns milliseconds per phase and the number
+ * of intervals (launch groups) per phase since the last read, then resets.
+ * Phases: 0 analysis, 1 symbolic rows, 2 scan, 3 numeric rows, 4 heavy rows,
+ * 5 partition, 6 backward, 7 mcl.  ms and count have SPGEMM_NUM_PHASES
+ * entries (host). */
+#define SPGEMM_NUM_PHASES 8
+spgemm_status spgemm_set_timing(spgemm_handle* h, int32_t enable);
+spgemm_status spgemm_read_timing(spgemm_handle* h, double* ms, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRIDENT_SPGEMM_H */

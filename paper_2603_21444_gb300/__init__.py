@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) hot path of the trident distributed SpGEMM (arXiv 2603.21444).
+
+The local CSR product C = A B (symbolic + numeric, row-binned), the ordered
+sum of trident partial products, the batched trident grid on one GPU and the
+autograd backward, all computed by hand-written CUDA kernels behind the C ABI
+in include/trident_spgemm.h.  PyTorch supplies device memory and streams.
+"""
+from .api import (BatchPlan, DeviceCSR, Handle, batched, default_handle, default_tune, merge,  # noqa: F401
+                  numeric_into, spgemm, symbolic)

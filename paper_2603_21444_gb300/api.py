@@ -1,0 +1,268 @@
+"""Python front end of the trident SpGEMM library.
+
+PyTorch supplies device memory and streams; every step runs in the CUDA
+library through the C ABI (``_abi``).  There is no CPU fallback: without a
+GPU and the built library these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import CsrIn, CsrOut, Tune, check
+
+_DT = {torch.float32: _abi.F32, torch.float64: _abi.F64}
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix in device memory: int32 row_ptr / col, float32 or float64 val."""
+
+    nrows: int
+    ncols: int
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor | None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def dtype(self):
+        return self.val.dtype if self.val is not None else None
+
+    @staticmethod
+    def from_host(host, device="cuda", dtype=None, pin: bool = False) -> "DeviceCSR":
+        """Copy a host CSR (anything with nrows, ncols, rowptr, col, val numpy arrays)."""
+        rp = torch.from_numpy(np.ascontiguousarray(host.rowptr, dtype=np.int32))
+        col = torch.from_numpy(np.ascontiguousarray(host.col, dtype=np.int32))
+        val = torch.from_numpy(np.ascontiguousarray(host.val))
+        if dtype is not None:
+            val = val.to(dtype)
+        if pin:
+            rp, col, val = rp.pin_memory(), col.pin_memory(), val.pin_memory()
+        nb = pin
+        return DeviceCSR(int(host.nrows), int(host.ncols), rp.to(device, non_blocking=nb),
+                         col.to(device, non_blocking=nb), val.to(device, non_blocking=nb))
+
+    def to_host(self):
+        """(rowptr int64, col int32, val) numpy arrays."""
+        return (self.row_ptr.cpu().numpy().astype(np.int64), self.col.cpu().numpy(),
+                None if self.val is None else self.val.cpu().numpy())
+
+    def as_in(self) -> CsrIn:
+        return CsrIn(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                     self.col.data_ptr() if self.nnz else None,
+                     self.val.data_ptr() if (self.val is not None and self.nnz) else None)
+
+    def as_out(self) -> CsrOut:
+        return CsrOut(self.nrows, self.ncols, self.row_ptr.data_ptr(), self.col.data_ptr() or None,
+                      (self.val.data_ptr() or None) if self.val is not None else None)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t not in _DT:
+        raise TypeError(f"unsupported value dtype {t}")
+    return _DT[t]
+
+
+def default_tune() -> Tune:
+    t = Tune()
+    check(_abi.lib().spgemm_default_tune(ctypes.byref(t)), "spgemm_default_tune")
+    return t
+
+
+class Handle:
+    """Owns one library handle (workspace, bin lists, instrumentation)."""
+
+    def __init__(self):
+        self._h = ctypes.c_void_p()
+        check(_abi.lib().spgemm_create(ctypes.byref(self._h)), "spgemm_create")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _abi.lib().spgemm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tune(self, tune: Tune | None):
+        check(_abi.lib().spgemm_set_tune(self._h, ctypes.byref(tune) if tune is not None else None),
+              "spgemm_set_tune")
+
+    def get_tune(self) -> Tune:
+        t = Tune()
+        check(_abi.lib().spgemm_get_tune(self._h, ctypes.byref(t)), "spgemm_get_tune")
+        return t
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int64()
+        check(_abi.lib().spgemm_launch_count(self._h, ctypes.byref(c)), "spgemm_launch_count")
+        return int(c.value)
+
+    def device_status(self) -> int:
+        return int(_abi.lib().spgemm_device_status(self._h))
+
+    def set_timing(self, on: bool):
+        check(_abi.lib().spgemm_set_timing(self._h, 1 if on else 0), "spgemm_set_timing")
+
+    def read_timing(self):
+        """(ms per phase, intervals per phase) since the last read."""
+        ms = (ctypes.c_double * _abi.NUM_PHASES)()
+        cnt = (ctypes.c_int64 * _abi.NUM_PHASES)()
+        check(_abi.lib().spgemm_read_timing(self._h, ms, cnt), "spgemm_read_timing")
+        return list(ms), list(cnt)
+
+
+_default = {}
+
+
+def default_handle() -> Handle:
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Handle()
+    return _default[dev]
+
+
+# -------------------------------------------------------------- the product
+
+def symbolic(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None):
+    """Row pointer of C = A B and nnz(C) (one host synchronisation)."""
+    h = handle or default_handle()
+    rp = torch.empty(A.nrows + 1, dtype=torch.int32, device=A.row_ptr.device)
+    nnz = ctypes.c_int64()
+    a, b = A.as_in(), B.as_in()
+    check(_abi.lib().spgemm_symbolic(h.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(rp.data_ptr()),
+                                     ctypes.byref(nnz), _stream(stream)), "spgemm_symbolic")
+    return rp, int(nnz.value)
+
+
+def numeric_into(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """Fill C.col / C.val given C.row_ptr from ``symbolic`` (asynchronous)."""
+    h = handle or default_handle()
+    a, b, c = A.as_in(), B.as_in(), C.as_out()
+    check(_abi.lib().spgemm_numeric(h.ptr, _dtype_code(A.val.dtype), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c), _stream(stream)), "spgemm_numeric")
+    return C
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """C = A B (symbolic, allocate, numeric)."""
+    if A.val is None or B.val is None or A.val.dtype != B.val.dtype:
+        raise TypeError("A and B need values of one dtype")
+    rp, nnz = symbolic(A, B, handle, stream)
+    dev = A.row_ptr.device
+    C = DeviceCSR(A.nrows, B.ncols, rp, torch.empty(nnz, dtype=torch.int32, device=dev),
+                  torch.empty(nnz, dtype=A.val.dtype, device=dev))
+    return numeric_into(A, B, C, handle, stream)
+
+
+# ------------------------------------------------------------------ merge
+
+def merge(parts: list[DeviceCSR], handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """C = parts[0] + parts[1] + ... (union pattern, added in part order)."""
+    h = handle or default_handle()
+    n = len(parts)
+    arr = (CsrIn * n)(*[p.as_in() for p in parts])
+    m, ncols, dt = parts[0].nrows, parts[0].ncols, parts[0].val.dtype
+    dev = parts[0].row_ptr.device
+    rp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    out = CsrOut(m, ncols, rp.data_ptr(), None, None)
+    nnz = ctypes.c_int64()
+    check(_abi.lib().spgemm_merge(h.ptr, _dtype_code(dt), n, arr, ctypes.byref(out), ctypes.byref(nnz),
+                                  _stream(stream)), "spgemm_merge(size)")
+    C = DeviceCSR(m, ncols, rp, torch.empty(nnz.value, dtype=torch.int32, device=dev),
+                  torch.empty(nnz.value, dtype=dt, device=dev))
+    out = C.as_out()
+    if nnz.value:
+        check(_abi.lib().spgemm_merge(h.ptr, _dtype_code(dt), n, arr, ctypes.byref(out), None, _stream(stream)),
+              "spgemm_merge(fill)")
+    return C
+
+
+# ---------------------------------------------------------------- batched
+
+class BatchPlan:
+    """Marshalled arguments of one batched problem (built once, called often)."""
+
+    def __init__(self, As: list[DeviceCSR], Bs: list[DeviceCSR], group_ptr: list[int] | None = None):
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need equally many A and B instances")
+        self.As, self.Bs = As, Bs
+        self.ninst = len(As)
+        self.group_ptr = list(group_ptr) if group_ptr is not None else list(range(self.ninst + 1))
+        self.ngroups = len(self.group_ptr) - 1
+        self.dtype = As[0].val.dtype
+        self.a_arr = (CsrIn * self.ninst)(*[a.as_in() for a in As])
+        self.b_arr = (CsrIn * self.ninst)(*[b.as_in() for b in Bs])
+        self.gp = (ctypes.c_int32 * (self.ngroups + 1))(*self.group_ptr)
+        dev = As[0].row_ptr.device
+        self.C = []
+        for g in range(self.ngroups):
+            t = self.group_ptr[g]
+            self.C.append(DeviceCSR(As[t].nrows, Bs[t].ncols,
+                                    torch.empty(As[t].nrows + 1, dtype=torch.int32, device=dev),
+                                    torch.empty(0, dtype=torch.int32, device=dev),
+                                    torch.empty(0, dtype=self.dtype, device=dev)))
+        self.nnz = None
+
+    def _out(self, sizing: bool):
+        outs = (CsrOut * self.ngroups)()
+        for g, C in enumerate(self.C):
+            outs[g] = CsrOut(C.nrows, C.ncols, C.row_ptr.data_ptr(), None, None) if sizing else C.as_out()
+        return outs
+
+    def size(self, handle: Handle | None = None, tune: Tune | None = None, stream=None):
+        h = handle or default_handle()
+        nnz = (ctypes.c_int64 * self.ngroups)()
+        outs = self._out(True)
+        check(_abi.lib().spgemm_batched(h.ptr, _dtype_code(self.dtype), self.ninst, self.a_arr, self.b_arr,
+                                        self.ngroups, self.gp, outs, nnz,
+                                        ctypes.byref(tune) if tune is not None else None, _stream(stream)),
+              "spgemm_batched(size)")
+        self.nnz = [int(x) for x in nnz]
+        return self.nnz
+
+    def allocate(self):
+        dev = self.As[0].row_ptr.device
+        for C, n in zip(self.C, self.nnz):
+            if C.col.numel() != n:
+                C.col = torch.empty(n, dtype=torch.int32, device=dev)
+                C.val = torch.empty(n, dtype=self.dtype, device=dev)
+
+    def fill(self, handle: Handle | None = None, tune: Tune | None = None, stream=None):
+        h = handle or default_handle()
+        outs = self._out(False)
+        check(_abi.lib().spgemm_batched(h.ptr, _dtype_code(self.dtype), self.ninst, self.a_arr, self.b_arr,
+                                        self.ngroups, self.gp, outs, None,
+                                        ctypes.byref(tune) if tune is not None else None, _stream(stream)),
+              "spgemm_batched(fill)")
+        return self.C
+
+    def run(self, handle: Handle | None = None, tune: Tune | None = None, stream=None):
+        self.size(handle, tune, stream)
+        self.allocate()
+        return self.fill(handle, tune, stream)
+
+
+def batched(As, Bs, group_ptr=None, handle: Handle | None = None, tune: Tune | None = None, stream=None):
+    """Outputs C[g] = sum over the group's instances (in order) of A[t] B[t]."""
+    return BatchPlan(As, Bs, group_ptr).run(handle, tune, stream)

@@ -1,0 +1,701 @@
+// C ABI of the trident SpGEMM library: handles, argument checking, workspace,
+// and the host-side flow of symbolic / numeric / merge / batched calls.
+//
+// Flow of one call (all on the caller's stream):
+//   descriptors -> device (one small copy)
+//   [validate]      k_validate per input matrix
+//   analysis        k_analysis (u_i, A-row length -> bin), k_bin_offsets,
+//                   k_bin_fill (per-bin unit lists)
+//   sizing call     k_sym_rows per bin + k_sym_heavy, k_scan_* (counts ->
+//                   exclusive sums), k_rowptr (per-group row_ptr, nnz),
+//                   one device->host copy and one stream synchronisation
+//   fill call       k_num_rows per non-empty bin + k_num_heavy
+// A fill call that follows the sizing call of the same problem on the same
+// handle reuses its bin lists (no second analysis, no host round trip).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "trident_spgemm.h"
+
+using namespace tsg;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct PhaseEvent {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+constexpr int kNumPhases = SPGEMM_NUM_PHASES;
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+}  // namespace
+
+struct spgemm_handle {
+    int device = 0;
+    int sms = 0;
+    spgemm_tune tune{};
+    DevBuf units;   // bin_of | list | counts | ex
+    long long units_cap = -1;
+    DevBuf small;
+    DevBuf dense;
+    void* pinned = nullptr;
+    size_t pinned_n = 0;
+    // plan cache (bin lists of the last sizing call)
+    uint64_t plan_sig = 0;
+    bool plan_valid = false;
+    std::vector<int> plan_hist;
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<PhaseEvent> pending;
+    std::vector<cudaEvent_t> spare;
+    cudaStream_t last_stream = nullptr;
+    int occ_wpb = -1;
+    int occ_sym[kNumVariants];
+    int occ_num[2][kNumVariants];
+    std::vector<cudaStream_t> streams_used;
+};
+
+namespace {
+
+spgemm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SPGEMM_OK;
+    if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OOM;
+    return SPGEMM_ERR_CUDA;
+}
+
+#define TSG_CHECK(expr)                                   \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_status(e_);    \
+    } while (0)
+
+#define TSG_TRY(expr)                                     \
+    do {                                                  \
+        spgemm_status s_ = (expr);                        \
+        if (s_ != SPGEMM_OK) return s_;                   \
+    } while (0)
+
+spgemm_status grow(DevBuf& b, size_t bytes, cudaStream_t zero_on = nullptr, bool zero = false) {
+    if (b.n >= bytes) return SPGEMM_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    size_t n = std::max(bytes, size_t(1) << 16);
+    if (cudaMalloc(&b.p, n) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return SPGEMM_ERR_OOM;
+    }
+    b.n = n;
+    if (zero) TSG_CHECK(cudaMemsetAsync(b.p, 0, n, zero_on));
+    return SPGEMM_OK;
+}
+
+spgemm_status grow_pinned(spgemm_handle* h, size_t bytes) {
+    if (h->pinned_n >= bytes) return SPGEMM_OK;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    h->pinned_n = 0;
+    size_t n = std::max(bytes, size_t(4096));
+    if (cudaMallocHost(&h->pinned, n) != cudaSuccess) {
+        cudaGetLastError();
+        return SPGEMM_ERR_OOM;
+    }
+    h->pinned_n = n;
+    return SPGEMM_OK;
+}
+
+void default_tune(spgemm_tune* t) {
+    std::memset(t, 0, sizeof(*t));
+    const int upper[9] = {32, 64, 128, 256, 512, 1024, 2048, 4096, 8192};
+    t->num_bins = 9;
+    for (int b = 0; b < 9; ++b) {
+        t->bin_upper[b] = upper[b];
+        t->bin_kernel[b] = b;
+    }
+    t->accumulator = SPGEMM_ACC_SORT;
+    t->warps_per_block = 8;
+    t->validate = 0;
+}
+
+spgemm_status check_tune(const spgemm_tune* t) {
+    if (t->num_bins < 1 || t->num_bins > SPGEMM_MAX_BINS) return SPGEMM_ERR_INVALID_ARG;
+    if (t->accumulator != SPGEMM_ACC_SORT) return SPGEMM_ERR_INVALID_ARG;
+    if (t->warps_per_block < 1 || t->warps_per_block > 16) return SPGEMM_ERR_INVALID_ARG;
+    for (int b = 0; b < t->num_bins; ++b) {
+        const int v = t->bin_kernel[b];
+        if (v < 0 || v >= kNumVariants) return SPGEMM_ERR_INVALID_ARG;
+        if (t->bin_upper[b] < 1 || t->bin_upper[b] > variant_cap(v)) return SPGEMM_ERR_INVALID_ARG;
+        if (b > 0 && t->bin_upper[b] <= t->bin_upper[b - 1]) return SPGEMM_ERR_INVALID_ARG;
+    }
+    return SPGEMM_OK;
+}
+
+BinTable bins_of(const spgemm_tune& t) {
+    BinTable bt{};
+    bt.nbins = t.num_bins;
+    for (int b = 0; b < t.num_bins; ++b) {
+        bt.upper[b] = t.bin_upper[b];
+        bt.amax[b] = variant_cap(t.bin_kernel[b]) / 2;
+    }
+    return bt;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct PhaseScope {
+    spgemm_handle* h;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseScope(spgemm_handle* h_, int phase_, cudaStream_t s_) : h(h_), phase(phase_), s(s_) {
+        if (!h->timing) return;
+        a = take();
+        b = take();
+        if (a) cudaEventRecord(a, s);
+    }
+    cudaEvent_t take() {
+        if (!h->spare.empty()) {
+            cudaEvent_t e = h->spare.back();
+            h->spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    ~PhaseScope() {
+        if (!h->timing) return;
+        if (a && b) {
+            cudaEventRecord(b, s);
+            h->pending.push_back({phase, a, b});
+        } else {
+            if (a) h->spare.push_back(a);
+            if (b) h->spare.push_back(b);
+        }
+    }
+};
+
+void occupancy(spgemm_handle* h, int wpb) {
+    if (h->occ_wpb == wpb) return;
+    for (int v = 0; v < kNumVariants; ++v) {
+        h->occ_sym[v] = std::max(1, sym_blocks_per_sm(v, wpb));
+        h->occ_num[0][v] = std::max(1, num_blocks_per_sm(v, 0, wpb));
+        h->occ_num[1][v] = std::max(1, num_blocks_per_sm(v, 1, wpb));
+    }
+    h->occ_wpb = wpb;
+}
+
+int teams_per_block(int v, int wpb) { return variant_team(v) == 32 ? wpb : 1; }
+
+void note_stream(spgemm_handle* h, cudaStream_t s) {
+    h->last_stream = s;
+    if (std::find(h->streams_used.begin(), h->streams_used.end(), s) == h->streams_used.end())
+        h->streams_used.push_back(s);
+}
+
+struct Validate {
+    const int* rp;
+    const int* col;
+    int nrows, ncols, nnz;
+};
+
+// One call of the engine: product (merge == false) or ordered sum of partials.
+spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<InstDev>& inst,
+                  const std::vector<GroupDev>& groups, bool sizing, int64_t* c_nnz, const spgemm_tune& tune,
+                  const std::vector<Validate>& checks, cudaStream_t st) {
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    note_stream(h, st);
+    const int ngroups = (int)groups.size();
+    const int ninst = (int)inst.size();
+    std::vector<long long> unit_base(ngroups + 1);
+    long long U = 0;
+    int max_ncols = 1;
+    for (int g = 0; g < ngroups; ++g) {
+        unit_base[g] = U;
+        U += groups[g].nrows;
+        max_ncols = std::max(max_ncols, groups[g].ncols);
+    }
+    unit_base[ngroups] = U;
+    if (U >= (1ll << 31) - 1) return SPGEMM_ERR_UNSUPPORTED;
+    const int nb = tune.num_bins;
+    const int nslots = nb + 2;  // regular bins, heavy, empty
+
+    if (sizing) {
+        // row_ptr of groups without rows is the single entry 0
+        for (int g = 0; g < ngroups; ++g)
+            if (groups[g].nrows == 0) TSG_CHECK(cudaMemsetAsync(groups[g].crp, 0, sizeof(int), st));
+    }
+    if (U == 0) {
+        if (sizing && c_nnz)
+            for (int g = 0; g < ngroups; ++g) c_nnz[g] = 0;
+        return SPGEMM_OK;
+    }
+
+    // ---- workspace
+    if (U > h->units_cap) {
+        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1));
+        TSG_TRY(grow(h->units, bytes));
+        h->units_cap = U;
+        h->plan_valid = false;
+    }
+    char* ub = static_cast<char*>(h->units.p);
+    unsigned char* d_bin_of = reinterpret_cast<unsigned char*>(ub);
+    int* d_list = reinterpret_cast<int*>(ub + align16(h->units_cap));
+    int* d_counts = reinterpret_cast<int*>(ub + align16(h->units_cap) + align16(4 * h->units_cap));
+    long long* d_ex =
+        reinterpret_cast<long long*>(ub + align16(h->units_cap) + 2 * align16(4 * h->units_cap));
+
+    const long long nblk = scan_blocks(U);
+    size_t o_hist = 0;
+    size_t o_off = o_hist + align16(4 * (kMaxBins + 2));
+    size_t o_cur = o_off + align16(4 * (kMaxBins + 3));
+    size_t o_status = o_cur + align16(4 * (kMaxBins + 2));
+    size_t o_bsum = o_status + 16;
+    size_t o_nnz = o_bsum + align16(8 * nblk);
+    size_t o_ubase = o_nnz + align16(8 * ngroups);
+    size_t o_inst = o_ubase + align16(8 * (ngroups + 1));
+    size_t o_groups = o_inst + align16(sizeof(InstDev) * ninst);
+    size_t small_bytes = o_groups + align16(sizeof(GroupDev) * ngroups);
+    if (h->small.n < small_bytes) h->plan_valid = false;
+    TSG_TRY(grow(h->small, small_bytes));
+    char* sb = static_cast<char*>(h->small.p);
+    int* d_hist = reinterpret_cast<int*>(sb + o_hist);
+    int* d_off = reinterpret_cast<int*>(sb + o_off);
+    int* d_cur = reinterpret_cast<int*>(sb + o_cur);
+    unsigned* d_status = reinterpret_cast<unsigned*>(sb + o_status);
+    long long* d_bsum = reinterpret_cast<long long*>(sb + o_bsum);
+    long long* d_nnz = reinterpret_cast<long long*>(sb + o_nnz);
+    long long* d_ubase = reinterpret_cast<long long*>(sb + o_ubase);
+    InstDev* d_inst = reinterpret_cast<InstDev*>(sb + o_inst);
+    GroupDev* d_groups = reinterpret_cast<GroupDev*>(sb + o_groups);
+
+    const size_t pinned_bytes = align16(8 * ngroups) + align16(4 * (kMaxBins + 2)) + 16;
+    TSG_TRY(grow_pinned(h, pinned_bytes));
+    long long* p_nnz = static_cast<long long*>(h->pinned);
+    int* p_hist = reinterpret_cast<int*>(static_cast<char*>(h->pinned) + align16(8 * ngroups));
+    unsigned* p_status =
+        reinterpret_cast<unsigned*>(static_cast<char*>(h->pinned) + align16(8 * ngroups) + align16(4 * (kMaxBins + 2)));
+
+    // ---- descriptors (pageable source: the copy is staged before the call returns)
+    {
+        std::vector<char> stage(small_bytes - o_ubase);
+        std::memcpy(stage.data(), unit_base.data(), 8 * (ngroups + 1));
+        if (ninst) std::memcpy(stage.data() + (o_inst - o_ubase), inst.data(), sizeof(InstDev) * ninst);
+        std::memcpy(stage.data() + (o_groups - o_ubase), groups.data(), sizeof(GroupDev) * ngroups);
+        TSG_CHECK(cudaMemcpyAsync(sb + o_ubase, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
+    }
+    TSG_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+
+    // ---- plan signature (input patterns, output row_ptr, bins)
+    uint64_t sig = 1469598103934665603ull;
+    sig = fnv(sig, &merge, sizeof(merge));
+    for (const InstDev& I : inst) {
+        const void* ptrs[4] = {I.arp, I.acol, I.brp, I.bcol};
+        sig = fnv(sig, ptrs, sizeof(ptrs));
+    }
+    for (const GroupDev& G : groups) {
+        const int shape[4] = {G.inst_begin, G.inst_count, G.nrows, G.ncols};
+        sig = fnv(sig, shape, sizeof(shape));
+        sig = fnv(sig, &G.crp, sizeof(G.crp));
+    }
+    sig = fnv(sig, tune.bin_upper, sizeof(int) * nb);
+    sig = fnv(sig, tune.bin_kernel, sizeof(int) * nb);
+
+    if (tune.validate) {
+        // nothing else may read a bad input: check, wait, then proceed
+        for (const Validate& v : checks) {
+            TSG_CHECK(launch_validate(v.rp, v.col, v.nrows, v.ncols, v.nnz, d_status, st));
+            ++h->launches;
+        }
+        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        if (*p_status & kStatusNotCanonical) {
+            h->plan_valid = false;
+            return SPGEMM_ERR_NOT_CANONICAL;
+        }
+    }
+
+    const bool reuse = !sizing && h->plan_valid && h->plan_sig == sig;
+    if (!reuse) {
+        h->plan_valid = false;
+        PhaseScope ps(h, 0, st);
+        TSG_CHECK(cudaMemsetAsync(d_hist, 0, 4 * nslots, st));
+        AnalysisArgs aa;
+        aa.inst = d_inst;
+        aa.groups = d_groups;
+        aa.unit_base = d_ubase;
+        aa.ngroups = ngroups;
+        aa.nunits = U;
+        aa.merge = merge ? 1 : 0;
+        aa.bt = bins_of(tune);
+        aa.bin_of = d_bin_of;
+        aa.hist = d_hist;
+        aa.counts = d_counts;
+        aa.sizing = sizing ? 1 : 0;
+        TSG_CHECK(launch_analysis(aa, st));
+        TSG_CHECK(launch_bin_offsets(d_hist, d_off, d_cur, nslots, st));
+        TSG_CHECK(launch_bin_fill(d_bin_of, U, d_off, d_cur, d_list, st));
+        h->launches += 3;
+    }
+
+    occupancy(h, tune.warps_per_block);
+    const int wpb = tune.warps_per_block;
+    RowLaunchArgs la;
+    la.inst = d_inst;
+    la.groups = d_groups;
+    la.unit_base = d_ubase;
+    la.ngroups = ngroups;
+    la.list = d_list;
+    la.bin_off = d_off;
+    la.merge = merge ? 1 : 0;
+    la.status = d_status;
+    la.counts = d_counts;
+    const int chunk = heavy_chunk_for(max_ncols);
+
+    if (sizing) {
+        {
+            PhaseScope ps(h, 1, st);
+            for (int b = 0; b < nb; ++b) {
+                const int v = tune.bin_kernel[b];
+                la.bin = b;
+                TSG_CHECK(launch_sym_rows(v, la, h->sms * h->occ_sym[v], wpb, st));
+                ++h->launches;
+            }
+        }
+        {
+            PhaseScope ps(h, 4, st);
+            la.bin = nb;
+            TSG_CHECK(launch_sym_heavy(la, h->sms, chunk, st));
+            ++h->launches;
+        }
+        {
+            PhaseScope ps(h, 2, st);
+            TSG_CHECK(cudaMemsetAsync(d_nnz, 0, 8 * ngroups, st));
+            TSG_CHECK(launch_scan(d_counts, U, d_bsum, d_ex, st));
+            TSG_CHECK(launch_rowptr(d_groups, d_ubase, ngroups, U, d_ex, d_nnz, st));
+            h->launches += 4;
+        }
+        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8 * ngroups, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        const unsigned status = *p_status;
+        if (status & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
+        if (status & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;
+        if (status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+        bool overflow = false;
+        for (int g = 0; g < ngroups; ++g) {
+            if (c_nnz) c_nnz[g] = p_nnz[g];
+            if (p_nnz[g] > 2147483647ll) overflow = true;
+        }
+        if (overflow) return SPGEMM_ERR_INDEX_OVERFLOW;
+        h->plan_hist.assign(p_hist, p_hist + nslots);
+        h->plan_sig = sig;
+        h->plan_valid = true;
+        return SPGEMM_OK;
+    }
+
+    // ---- fill call
+    std::vector<int> hist;
+    if (reuse) {
+        hist = h->plan_hist;
+    } else {
+        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        hist.assign(p_hist, p_hist + nslots);
+    }
+    if (hist[nb] > 0) {
+        PhaseScope ps(h, 4, st);
+        const int blocks = std::min(hist[nb], h->sms);
+        const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
+        TSG_TRY(grow(h->dense, (size_t)blocks * chunk * esz, st, true));
+        // blocks beyond the allocation would share slots: size the grid to it
+        const int slots = (int)std::min<size_t>(blocks, h->dense.n / ((size_t)chunk * esz));
+        la.bin = nb;
+        TSG_CHECK(launch_num_heavy(dtype, la, h->dense.p, slots, chunk, st));
+        ++h->launches;
+    }
+    {
+        PhaseScope ps(h, 3, st);
+        for (int b = 0; b < nb; ++b) {
+            if (hist[b] == 0) continue;
+            const int v = tune.bin_kernel[b];
+            const int tpb = teams_per_block(v, wpb);
+            const long long need = (hist[b] + tpb - 1) / tpb;
+            const int blocks = (int)std::min<long long>(need, (long long)h->sms * h->occ_num[dtype][v]);
+            la.bin = b;
+            TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wpb, st));
+            ++h->launches;
+        }
+    }
+    if (tune.validate) {
+        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        if (*p_status & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
+        if (*p_status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+    }
+    return SPGEMM_OK;
+}
+
+bool csr_in_ok(const spgemm_csr_in* X, bool need_val) {
+    if (!X || X->nrows < 0 || X->ncols < 0 || X->nnz < 0 || !X->row_ptr) return false;
+    if (X->nnz > 0 && (!X->col_idx || (need_val && !X->val))) return false;
+    return true;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* spgemm_status_str(spgemm_status s) {
+    switch (s) {
+        case SPGEMM_OK: return "ok";
+        case SPGEMM_ERR_INVALID_ARG: return "invalid argument";
+        case SPGEMM_ERR_SHAPE: return "shape mismatch";
+        case SPGEMM_ERR_DTYPE: return "unknown dtype";
+        case SPGEMM_ERR_INDEX_OVERFLOW: return "output nnz exceeds int32";
+        case SPGEMM_ERR_OOM: return "out of device memory";
+        case SPGEMM_ERR_CUDA: return "CUDA runtime error";
+        case SPGEMM_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+        case SPGEMM_ERR_HASH_OVERFLOW: return "accumulator overflow";
+        case SPGEMM_ERR_NOT_CANONICAL: return "input is not a valid CSR matrix";
+        case SPGEMM_ERR_INTERNAL: return "device consistency check failed";
+        case SPGEMM_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* spgemm_version(void) { return "trident-spgemm-gb300 0.1 (sm_103a)"; }
+
+spgemm_status spgemm_default_tune(spgemm_tune* t) {
+    if (!t) return SPGEMM_ERR_INVALID_ARG;
+    default_tune(t);
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_create(spgemm_handle** out) {
+    if (!out) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SPGEMM_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return SPGEMM_ERR_CUDA;
+    }
+    spgemm_handle* h = new (std::nothrow) spgemm_handle();
+    if (!h) return SPGEMM_ERR_OOM;
+    h->device = dev;
+    h->sms = sms;
+    default_tune(&h->tune);
+    *out = h;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_destroy(spgemm_handle* h) {
+    if (!h) return SPGEMM_OK;
+    for (cudaStream_t s : h->streams_used) cudaStreamSynchronize(s);
+    for (const PhaseEvent& p : h->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : h->spare) cudaEventDestroy(e);
+    if (h->units.p) cudaFree(h->units.p);
+    if (h->small.p) cudaFree(h->small.p);
+    if (h->dense.p) cudaFree(h->dense.p);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_set_tune(spgemm_handle* h, const spgemm_tune* t) {
+    if (!h) return SPGEMM_ERR_INVALID_ARG;
+    if (!t) {
+        default_tune(&h->tune);
+        return SPGEMM_OK;
+    }
+    TSG_TRY(check_tune(t));
+    h->tune = *t;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_get_tune(const spgemm_handle* h, spgemm_tune* t) {
+    if (!h || !t) return SPGEMM_ERR_INVALID_ARG;
+    *t = h->tune;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B, int32_t* c_row_ptr,
+                              int64_t* c_nnz, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(A, false) || !csr_in_ok(B, false) || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+    if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, c_row_ptr, nullptr, nullptr}};
+    std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
+                                 {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
+    return run(h, 0, false, inst, groups, true, c_nnz, h->tune, checks, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                             spgemm_csr_out* C, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(A, true) || !csr_in_ok(B, true) || !C || !C->row_ptr) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val}};
+    std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
+                                 {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
+    return run(h, dtype, false, inst, groups, false, nullptr, h->tune, checks,
+               reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_merge(spgemm_handle* h, spgemm_dtype dtype, int32_t nparts, const spgemm_csr_in* parts,
+                           spgemm_csr_out* C, int64_t* c_nnz, spgemm_stream_t stream) {
+    if (!h || !parts || !C || !C->row_ptr || nparts < 1 || nparts > kMaxGroupInst) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    const bool sizing = C->col_idx == nullptr;
+    if (sizing && !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+    std::vector<InstDev> inst;
+    std::vector<Validate> checks;
+    for (int t = 0; t < nparts; ++t) {
+        const spgemm_csr_in* P = parts + t;
+        if (!csr_in_ok(P, !sizing)) return SPGEMM_ERR_INVALID_ARG;
+        if (P->nrows != C->nrows || P->ncols != C->ncols) return SPGEMM_ERR_SHAPE;
+        inst.push_back({nullptr, nullptr, nullptr, P->row_ptr, P->col_idx, P->val});
+        checks.push_back({P->row_ptr, P->col_idx, P->nrows, P->ncols, P->nnz});
+    }
+    if (!sizing && !C->val) return SPGEMM_ERR_INVALID_ARG;
+    std::vector<GroupDev> groups{{0, nparts, C->nrows, C->ncols, C->row_ptr, C->col_idx, C->val}};
+    return run(h, dtype, true, inst, groups, sizing, c_nnz, h->tune, checks, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst, const spgemm_csr_in* A,
+                             const spgemm_csr_in* B, int32_t ngroups, const int32_t* group_ptr, spgemm_csr_out* C,
+                             int64_t* c_nnz, const spgemm_tune* tune, spgemm_stream_t stream) {
+    if (!h || ninst < 1 || ninst > (1 << 20) || !A || !B || !C) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (group_ptr == nullptr) {
+        if (ngroups != ninst) return SPGEMM_ERR_INVALID_ARG;
+    } else {
+        if (ngroups < 1 || group_ptr[0] != 0 || group_ptr[ngroups] != ninst) return SPGEMM_ERR_INVALID_ARG;
+    }
+    spgemm_tune tn = h->tune;
+    if (tune) {
+        TSG_TRY(check_tune(tune));
+        tn = *tune;
+    }
+    const bool sizing = c_nnz != nullptr;
+    std::vector<InstDev> inst;
+    std::vector<GroupDev> groups;
+    std::vector<Validate> checks;
+    inst.reserve(ninst);
+    groups.reserve(ngroups);
+    for (int g = 0; g < ngroups; ++g) {
+        const int t0 = group_ptr ? group_ptr[g] : g;
+        const int t1 = group_ptr ? group_ptr[g + 1] : g + 1;
+        if (t1 <= t0 || t1 - t0 > kMaxGroupInst) return SPGEMM_ERR_INVALID_ARG;
+        const spgemm_csr_out& Cg = C[g];
+        if (!Cg.row_ptr) return SPGEMM_ERR_INVALID_ARG;
+        for (int t = t0; t < t1; ++t) {
+            if (!csr_in_ok(A + t, !sizing) || !csr_in_ok(B + t, !sizing)) return SPGEMM_ERR_INVALID_ARG;
+            if (A[t].ncols != B[t].nrows || A[t].nrows != Cg.nrows || B[t].ncols != Cg.ncols) return SPGEMM_ERR_SHAPE;
+        }
+        groups.push_back({t0, t1 - t0, Cg.nrows, Cg.ncols, Cg.row_ptr, sizing ? nullptr : Cg.col_idx,
+                          sizing ? nullptr : Cg.val});
+    }
+    for (int t = 0; t < ninst; ++t) {
+        inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val});
+        if (tn.validate) {
+            checks.push_back({A[t].row_ptr, A[t].col_idx, A[t].nrows, A[t].ncols, A[t].nnz});
+            checks.push_back({B[t].row_ptr, B[t].col_idx, B[t].nrows, B[t].ncols, B[t].nnz});
+        }
+    }
+    return run(h, dtype, false, inst, groups, sizing, c_nnz, tn, checks, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_launch_count(const spgemm_handle* h, int64_t* count) {
+    if (!h || !count) return SPGEMM_ERR_INVALID_ARG;
+    *count = h->launches;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_device_status(spgemm_handle* h) {
+    if (!h) return SPGEMM_ERR_INVALID_ARG;
+    if (!h->small.p) return SPGEMM_OK;
+    TSG_CHECK(cudaStreamSynchronize(h->last_stream));
+    const size_t o_status = align16(4 * (kMaxBins + 2)) + align16(4 * (kMaxBins + 3)) + align16(4 * (kMaxBins + 2));
+    unsigned st = 0;
+    TSG_CHECK(cudaMemcpy(&st, static_cast<char*>(h->small.p) + o_status, 4, cudaMemcpyDeviceToHost));
+    TSG_CHECK(cudaMemset(static_cast<char*>(h->small.p) + o_status, 0, 4));
+    if (st & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
+    if (st & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;
+    if (st & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_set_timing(spgemm_handle* h, int32_t enable) {
+    if (!h) return SPGEMM_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_read_timing(spgemm_handle* h, double* ms, int64_t* count) {
+    if (!h || !ms || !count) return SPGEMM_ERR_INVALID_ARG;
+    for (int p = 0; p < kNumPhases; ++p) {
+        ms[p] = 0.0;
+        count[p] = 0;
+    }
+    spgemm_status rc = SPGEMM_OK;
+    for (const PhaseEvent& e : h->pending) {
+        if (cudaEventSynchronize(e.b) == cudaSuccess) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) {
+                ms[e.phase] += t;
+                count[e.phase] += 1;
+            }
+        } else {
+            cudaGetLastError();
+            rc = SPGEMM_ERR_CUDA;
+        }
+        h->spare.push_back(e.a);
+        h->spare.push_back(e.b);
+    }
+    h->pending.clear();
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Shared device-side definitions of the trident SpGEMM library (sm_103a).
+//
+// Work model.  Every call is a set of GROUPS, each producing one output CSR.
+// A group owns one or more INSTANCES; instance t contributes A_t B_t (product
+// mode) or, in merge mode, is itself a partial C_t whose rows are taken as
+// they are.  A WORK UNIT is one output row (group g, row rho); units of all
+// groups are numbered consecutively (group g owns units
+// [unit_base[g], unit_base[g+1])).  Units are binned by their
+// intermediate-product count u and their A-row length, and each bin is run by
+// a kernel variant whose team (a warp or a whole block) holds up to CAP
+// products of a row on chip.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsg {
+
+// ---------------------------------------------------------------- descriptors
+
+struct InstDev {
+    const int* arp;     // A_t row_ptr (product mode); unused in merge mode
+    const int* acol;    // A_t col_idx
+    const void* aval;   // A_t values
+    const int* brp;     // B_t row_ptr (merge mode: the partial's row_ptr)
+    const int* bcol;    // B_t col_idx
+    const void* bval;   // B_t values
+};
+
+struct GroupDev {
+    int inst_begin;     // first instance of the group
+    int inst_count;     // number of instances (>= 1)
+    int nrows;          // output rows
+    int ncols;          // output columns
+    int* crp;           // output row_ptr (nrows + 1)
+    int* ccol;          // output col_idx
+    void* cval;         // output values
+};
+
+// kernel variants: team size and capacity (products per team)
+constexpr int kNumVariants = 9;
+__host__ __device__ constexpr int variant_team(int v) {
+    return v <= 4 ? 32 : (v == 5 ? 128 : (v == 6 ? 256 : 512));
+}
+__host__ __device__ constexpr int variant_per(int v) {
+    return v <= 4 ? (1 << v) : (v == 8 ? 16 : 8);
+}
+__host__ __device__ constexpr int variant_cap(int v) { return variant_team(v) * variant_per(v); }
+constexpr int kMaxCap = 8192;
+constexpr int kMaxBins = 12;
+constexpr int kMaxGroupInst = 64;
+
+struct BinTable {
+    int nbins;
+    int upper[kMaxBins];   // product-count upper bound per bin
+    int amax[kMaxBins];    // A-row length bound per bin (capacity / 2)
+};
+// bin ids: 0..nbins-1 regular, nbins = heavy, nbins + 1 = empty
+// (heavy and empty always follow the regular bins)
+
+// status bits latched by kernels
+enum : unsigned {
+    kStatusInternal = 1u,      // a row produced a different count than row_ptr says
+    kStatusHashOverflow = 2u,  // a probe sequence ran past the table size
+    kStatusNotCanonical = 4u,  // validation failed
+};
+
+// ------------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int pow2ceil(int x) {
+    return x <= 1 ? 1 : 1 << (32 - __clz(x - 1));
+}
+
+// group of a unit: last g with unit_base[g] <= unit
+__device__ __forceinline__ int unit_group(const long long* __restrict__ unit_base, int ngroups,
+                                          long long unit) {
+    if (ngroups == 1) return 0;
+    int lo = 0, hi = ngroups;  // unit_base[lo] <= unit < unit_base[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(unit_base + mid) <= unit) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Team primitives.  TEAM == 32: one warp is a team (several teams per
+// block); otherwise the whole block (blockDim.x == TEAM) is one team and
+// `scratch` points at >= 33 ints of shared memory private to the team.
+template <int TEAM>
+struct Team {
+    static __device__ __forceinline__ int rank() { return TEAM == 32 ? (threadIdx.x & 31) : threadIdx.x; }
+    static __device__ __forceinline__ void sync() {
+        if (TEAM == 32) __syncwarp(); else __syncthreads();
+    }
+    // exclusive prefix sum of v over the team; *total receives the sum
+    static __device__ __forceinline__ int scan_excl(int v, int* total, int* scratch) {
+        const int lane = threadIdx.x & 31;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (TEAM == 32) {
+            *total = __shfl_sync(0xffffffffu, x, 31);
+            return x - v;
+        } else {
+            const int warp = threadIdx.x >> 5;
+            constexpr int NW = TEAM / 32;
+            if (lane == 31) scratch[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                int w = lane < NW ? scratch[lane] : 0;
+                int z = w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, z, o);
+                    if (lane >= o) z += y;
+                }
+                if (lane < NW) scratch[lane] = z - w;
+                if (lane == 31) scratch[32] = z;
+            }
+            __syncthreads();
+            int r = scratch[warp] + x - v;
+            *total = scratch[32];
+            __syncthreads();
+            return r;
+        }
+    }
+    static __device__ __forceinline__ int sum(int v, int* scratch) {
+        int t;
+        scan_excl(v, &t, scratch);
+        return t;
+    }
+    // exclusive count of set flags and the total, for one flag per thread
+    static __device__ __forceinline__ int count_excl(bool f, int* total, int* scratch) {
+        if (TEAM == 32) {
+            unsigned b = __ballot_sync(0xffffffffu, f);
+            *total = __popc(b);
+            return __popc(b & lanemask_lt());
+        }
+        return scan_excl(f ? 1 : 0, total, scratch);
+    }
+};
+
+// Bucket of a column for a row with NB buckets: monotone in col, in [0, NB).
+struct Bucketer {
+    unsigned mul;
+    bool direct;
+    __device__ __forceinline__ void init(int ncols, int nb) {
+        direct = ncols <= nb;
+        mul = direct ? 0u : (unsigned)(((unsigned long long)nb << 32) / (unsigned)ncols);
+    }
+    __device__ __forceinline__ int operator()(int col) const {
+        return direct ? col : (int)__umulhi((unsigned)col, mul);
+    }
+};
+
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T add_rn(T a, T b);
+template <> __device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+
+}  // namespace tsg

@@ -1,0 +1,67 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace tsg {
+
+struct RowArgs;
+
+struct AnalysisArgs {
+    const InstDev* inst;
+    const GroupDev* groups;
+    const long long* unit_base;
+    int ngroups;
+    long long nunits;
+    int merge;
+    BinTable bt;
+    unsigned char* bin_of;
+    int* hist;      // nbins + 2 counters
+    int* counts;    // per-unit row nnz (empty rows written here when sizing)
+    int sizing;
+};
+
+// analysis + binning (rows_misc.cu)
+cudaError_t launch_analysis(const AnalysisArgs& a, cudaStream_t s);
+cudaError_t launch_bin_offsets(int* hist, int* off, int* cursor, int nslots, cudaStream_t s);
+cudaError_t launch_bin_fill(const unsigned char* bin_of, long long nunits, const int* off, int* cursor,
+                            int* list, cudaStream_t s);
+
+// scan of per-unit counts into per-group row_ptr (rows_misc.cu)
+long long scan_blocks(long long nunits);
+cudaError_t launch_scan(const int* counts, long long nunits, long long* bsum, long long* ex, cudaStream_t s);
+cudaError_t launch_rowptr(const GroupDev* groups, const long long* unit_base, int ngroups, long long nunits,
+                          const long long* ex, long long* nnz_out, cudaStream_t s);
+
+// input validation (rows_misc.cu)
+cudaError_t launch_validate(const int* rp, const int* col, int nrows, int ncols, int nnz, unsigned* status,
+                            cudaStream_t s);
+
+// row kernels
+struct RowLaunchArgs {
+    const InstDev* inst;
+    const GroupDev* groups;
+    const long long* unit_base;
+    int ngroups;
+    const int* list;
+    const int* bin_off;
+    int bin;
+    int merge;
+    unsigned* status;
+    int* counts;
+};
+int sym_smem_bytes(int variant, int warps_per_block);
+int num_smem_bytes(int variant, int dtype, int warps_per_block);
+int sym_blocks_per_sm(int variant, int warps_per_block);
+int num_blocks_per_sm(int variant, int dtype, int warps_per_block);
+cudaError_t launch_sym_rows(int variant, const RowLaunchArgs& a, int blocks, int warps_per_block, cudaStream_t s);
+cudaError_t launch_num_rows(int variant, int dtype, const RowLaunchArgs& a, int blocks, int warps_per_block,
+                            cudaStream_t s);
+cudaError_t launch_sym_heavy(const RowLaunchArgs& a, int blocks, int chunk, cudaStream_t s);
+cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& a, void* dense, int blocks, int chunk,
+                             cudaStream_t s);
+int heavy_chunk_for(int ncols);
+
+}  // namespace tsg

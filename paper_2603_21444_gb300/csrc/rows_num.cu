@@ -1,0 +1,69 @@
+// Numeric row kernels (deterministic sort accumulator) and the heavy-row
+// dense accumulator, for float and double values.
+#include "rows_launch.cuh"
+
+namespace tsg {
+
+template <typename T>
+static int num_smem_bytes_t(int variant, int wpb) {
+    int bytes = 0;
+    dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        bytes = NumLayout<SS::CAP, T>::bytes * (SS::TEAM == 32 ? wpb : 1);
+        return cudaSuccess;
+    });
+    return bytes;
+}
+
+int num_smem_bytes(int variant, int dtype, int wpb) {
+    return dtype == 1 ? num_smem_bytes_t<double>(variant, wpb) : num_smem_bytes_t<float>(variant, wpb);
+}
+
+template <typename T>
+static int num_blocks_per_sm_t(int variant, int wpb) {
+    int nb = 0;
+    dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+        nb = blocks_per_sm(k_num_rows<SS::TEAM, SS::PER, T>, threads, num_smem_bytes_t<T>(variant, wpb));
+        return cudaSuccess;
+    });
+    return nb;
+}
+
+int num_blocks_per_sm(int variant, int dtype, int wpb) {
+    return dtype == 1 ? num_blocks_per_sm_t<double>(variant, wpb) : num_blocks_per_sm_t<float>(variant, wpb);
+}
+
+template <typename T>
+static cudaError_t launch_num_rows_t(int variant, const RowLaunchArgs& l, int blocks, int wpb, cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    return dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+        const int smem = num_smem_bytes_t<T>(variant, wpb);
+        cudaFuncSetAttribute(k_num_rows<SS::TEAM, SS::PER, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_num_rows<SS::TEAM, SS::PER, T><<<blocks, threads, smem, s>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_num_rows(int variant, int dtype, const RowLaunchArgs& l, int blocks, int wpb, cudaStream_t s) {
+    return dtype == 1 ? launch_num_rows_t<double>(variant, l, blocks, wpb, s)
+                      : launch_num_rows_t<float>(variant, l, blocks, wpb, s);
+}
+
+cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& l, void* dense, int blocks, int chunk, cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    const int smem = (chunk / 32) * 4;
+    if (dtype == 1) {
+        cudaFuncSetAttribute(k_num_heavy<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_num_heavy<double><<<blocks, kHeavyThreads, smem, s>>>(a, reinterpret_cast<double*>(dense), chunk);
+    } else {
+        cudaFuncSetAttribute(k_num_heavy<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_num_heavy<float><<<blocks, kHeavyThreads, smem, s>>>(a, reinterpret_cast<float*>(dense), chunk);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tsg

@@ -1,0 +1,84 @@
+// Symbolic row kernels: per-row distinct-column counts (hash set per team),
+// plus the heavy-row bitmap counter.
+#include "rows_launch.cuh"
+
+namespace tsg {
+
+int sym_smem_bytes(int variant, int wpb) {
+    int bytes = 0;
+    dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        bytes = SymLayout<SS::CAP>::bytes * (SS::TEAM == 32 ? wpb : 1);
+        return cudaSuccess;
+    });
+    return bytes;
+}
+
+int sym_blocks_per_sm(int variant, int wpb) {
+    int nb = 0;
+    dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+        nb = blocks_per_sm(k_sym_rows<SS::TEAM, SS::PER>, threads, sym_smem_bytes(variant, wpb));
+        return cudaSuccess;
+    });
+    return nb;
+}
+
+cudaError_t launch_sym_rows(int variant, const RowLaunchArgs& l, int blocks, int wpb, cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    return dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+        const int smem = sym_smem_bytes(variant, wpb);
+        cudaFuncSetAttribute(k_sym_rows<SS::TEAM, SS::PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_sym_rows<SS::TEAM, SS::PER><<<blocks, threads, smem, s>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+// Heavy rows: one block per row, a bitmap of `chunk` columns per pass.
+__global__ void __launch_bounds__(kHeavyThreads, 1) k_sym_heavy(RowArgs a, int chunk) {
+    extern __shared__ __align__(16) unsigned bm[];
+    __shared__ int scratch[34];
+    const int words = chunk >> 5;
+    const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
+    for (int i = begin + blockIdx.x; i < end; i += gridDim.x) {
+        const int unit = __ldg(a.list + i);
+        const int g = unit_group(a.unit_base, a.ngroups, unit);
+        const GroupDev& G = a.groups[g];
+        const int rho = (int)(unit - a.unit_base[g]);
+        long long total = 0;
+        for (long long c0 = 0; c0 < G.ncols; c0 += chunk) {
+            for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+            __syncthreads();
+            int fresh = 0;
+            heavy_products<false, float>(a, G, rho, [&](int col, float) {
+                const unsigned rel = (unsigned)((long long)col - c0);
+                if (rel < (unsigned)chunk) {
+                    const unsigned bit = 1u << (rel & 31);
+                    if (!(atomicOr(bm + (rel >> 5), bit) & bit)) ++fresh;
+                }
+            });
+            total += Team<kHeavyThreads>::sum(fresh, scratch);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.counts[unit] = (int)total;
+    }
+}
+
+int heavy_chunk_for(int ncols) {
+    int c = 32;
+    while (c < ncols && c < kHeavyChunk) c <<= 1;
+    return c;
+}
+
+cudaError_t launch_sym_heavy(const RowLaunchArgs& l, int blocks, int chunk, cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    const int smem = (chunk / 32) * 4;
+    cudaFuncSetAttribute(k_sym_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_sym_heavy<<<blocks, kHeavyThreads, smem, s>>>(a, chunk);
+    return cudaGetLastError();
+}
+
+}  // namespace tsg

@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every symbol the public header
+declares; host-only entry points work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(spgemm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_21444_gb300 import _abi, build
+    build.build()
+    return _abi.lib()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("spgemm_symbolic", "spgemm_numeric", "spgemm_merge", "spgemm_batched", "spgemm_create",
+                     "spgemm_destroy", "spgemm_status_str"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2603_21444_gb300 import _abi
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _abi.SIGNATURES, f"binding lacks {name}"
+
+
+def test_host_only_calls(lib):
+    from paper_2603_21444_gb300 import _abi
+    assert lib.spgemm_status_str(0) == b"ok"
+    assert lib.spgemm_status_str(4) == b"output nnz exceeds int32"
+    assert b"sm_103a" in lib.spgemm_version()
+    t = _abi.Tune()
+    assert lib.spgemm_default_tune(ctypes.byref(t)) == 0
+    assert t.num_bins == 9 and list(t.bin_upper)[:9] == [32, 64, 128, 256, 512, 1024, 2048, 4096, 8192]
+    assert lib.spgemm_default_tune(None) == 1
+    assert lib.spgemm_destroy(None) == 0
+
+
+def test_null_handle_rejected(lib):
+    # argument checks happen before any CUDA call
+    assert lib.spgemm_symbolic(None, None, None, None, None, None) == 1
+    assert lib.spgemm_numeric(None, 1, None, None, None, None) == 1
+    assert lib.spgemm_merge(None, 1, 1, None, None, None, None) == 1
+    assert lib.spgemm_batched(None, 1, 1, None, None, 1, None, None, None, None, None) == 1
+
+
+def test_create_without_device_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    h = ctypes.c_void_p()
+    assert lib.spgemm_create(ctypes.byref(h)) == 6
+    assert not h.value
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2603_21444_gb300 import _abi
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_abi, "_lib", None)
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        _abi.lib()
