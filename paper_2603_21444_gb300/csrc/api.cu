@@ -228,8 +228,9 @@ struct Validate {
 
 // One call of the engine: product (merge == false) or ordered sum of partials.
 spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<InstDev>& inst,
-                  const std::vector<GroupDev>& groups, bool sizing, int64_t* c_nnz, const spgemm_tune& tune,
+                  std::vector<GroupDev> groups, bool sizing, int64_t* c_nnz, const spgemm_tune& tune,
                   const std::vector<Validate>& checks, cudaStream_t st) {
+    for (GroupDev& G : groups) G.ncols_inv = (1ull << 63) / (unsigned long long)std::max(G.ncols, 1);
     int dev = -1;
     TSG_CHECK(cudaGetDevice(&dev));
     if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
@@ -564,7 +565,7 @@ spgemm_status spgemm_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const sp
     if (!h || !csr_in_ok(A, false) || !csr_in_ok(B, false) || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
     if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
     std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
-    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, c_row_ptr, nullptr, nullptr}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, c_row_ptr, nullptr, nullptr, 0}};
     std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
     return run(h, 0, false, inst, groups, true, c_nnz, h->tune, checks, reinterpret_cast<cudaStream_t>(stream));
@@ -576,7 +577,7 @@ spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_
     if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
     if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
     std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
-    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val, 0}};
     std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
     return run(h, dtype, false, inst, groups, false, nullptr, h->tune, checks,
@@ -599,7 +600,7 @@ spgemm_status spgemm_merge(spgemm_handle* h, spgemm_dtype dtype, int32_t nparts,
         checks.push_back({P->row_ptr, P->col_idx, P->nrows, P->ncols, P->nnz});
     }
     if (!sizing && !C->val) return SPGEMM_ERR_INVALID_ARG;
-    std::vector<GroupDev> groups{{0, nparts, C->nrows, C->ncols, C->row_ptr, C->col_idx, C->val}};
+    std::vector<GroupDev> groups{{0, nparts, C->nrows, C->ncols, C->row_ptr, C->col_idx, C->val, 0}};
     return run(h, dtype, true, inst, groups, sizing, c_nnz, h->tune, checks, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -635,7 +636,7 @@ spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst
             if (A[t].ncols != B[t].nrows || A[t].nrows != Cg.nrows || B[t].ncols != Cg.ncols) return SPGEMM_ERR_SHAPE;
         }
         groups.push_back({t0, t1 - t0, Cg.nrows, Cg.ncols, Cg.row_ptr, sizing ? nullptr : Cg.col_idx,
-                          sizing ? nullptr : Cg.val});
+                          sizing ? nullptr : Cg.val, 0});
     }
     for (int t = 0; t < ninst; ++t) {
         inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val});

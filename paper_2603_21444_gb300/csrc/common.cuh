@@ -35,6 +35,7 @@ struct GroupDev {
     int* crp;           // output row_ptr (nrows + 1)
     int* ccol;          // output col_idx
     void* cval;         // output values
+    unsigned long long ncols_inv;  // floor(2^63 / ncols), for bucket maps
 };
 
 // kernel variants: team size and capacity (products per team)
@@ -150,12 +151,15 @@ struct Team {
 };
 
 // Bucket of a column for a row with NB buckets: monotone in col, in [0, NB).
+// With inv = floor(2^63 / ncols) and nb = 2^e <= 2^31, mul = floor(2^(32+e) /
+// ncols) = inv >> (31 - e) exactly, and col -> floor(col * mul / 2^32) maps
+// [0, ncols) monotonically onto [0, nb).
 struct Bucketer {
     unsigned mul;
     bool direct;
-    __device__ __forceinline__ void init(int ncols, int nb) {
+    __device__ __forceinline__ void init(int ncols, unsigned long long inv, int nb) {
         direct = ncols <= nb;
-        mul = direct ? 0u : (unsigned)(((unsigned long long)nb << 32) / (unsigned)ncols);
+        mul = direct ? 0u : (unsigned)(inv >> __clz(nb));  // shift 31 - e
     }
     __device__ __forceinline__ int operator()(int col) const {
         return direct ? col : (int)__umulhi((unsigned)col, mul);

@@ -5,13 +5,13 @@
 //
 //   meta    for every entry k of the row's A rows (all instances of the
 //           group, in order): a pointer to B row k, a_ik, and the exclusive
-//           prefix of |B_k|; this flattens the row's u products so product p
-//           is read by thread p mod TEAM (coalesced reads of each B row).
+//           prefix of |B_k|; this flattens the row's u products; thread r
+//           owns products [r*PER, r*PER + PER) and walks them in order.
 //   symbolic  the product columns go into a shared-memory hash set (linear
-//           probing, 2 * pow2ceil(u) slots); the count of first insertions
+//           probing, 4 * pow2ceil(u) slots); the count of first insertions
 //           is nnz(C_i).
 //   numeric   deterministic sort accumulator: each product is keyed by
-//           (column, p); a counting sort over NB = pow2ceil(u) buckets (the
+//           (column, p); a counting sort over NB = 2 pow2ceil(u) buckets (the
 //           bucket is a monotone function of the column) followed by a rank
 //           inside each bucket gives the products in (column, p) order; each
 //           run of equal columns is then added in p order, i.e. in ascending
@@ -106,11 +106,13 @@ __device__ __forceinline__ bool build_meta(const RowArgs& a, const GroupDev& G, 
 template <int CAP>
 struct SymLayout {
     static constexpr int MAXA = CAP / 2;
-    static constexpr int table = 0;                               // int[2 CAP]
-    static constexpr int m_bc = table + 8 * CAP;                  // const int*[MAXA]
+    static constexpr int TBL = 4 * CAP;                           // hash slots (load <= 1/4)
+    static constexpr int table = 0;                               // int[TBL]
+    static constexpr int m_bc = table + 4 * TBL;                  // const int*[MAXA]
     static constexpr int m_pre = m_bc + 8 * MAXA;                 // int[MAXA + 1]
     static constexpr int scratch = (m_pre + 4 * (MAXA + 1) + 15) & ~15;  // int[34]
     static constexpr int bytes = (scratch + 34 * 4 + 15) & ~15;
+    static_assert(bytes <= 227 * 1024, "team layout exceeds shared memory");
 };
 
 template <int TEAM, int PER>
@@ -134,17 +136,34 @@ __device__ __forceinline__ void sym_row(const RowArgs& a, int unit, char* sm) {
         }
         return;
     }
-    const int T2 = 2 * pow2ceil(u);
+    const int T2 = 4 * pow2ceil(u);
     const int shift = 32 - (31 - __clz(T2));
-    for (int i = r; i < T2; i += TEAM) table[i] = -1;
+    for (int i = 4 * r; i < T2; i += 4 * TEAM) *reinterpret_cast<int4*>(table + i) = make_int4(-1, -1, -1, -1);
+    // thread r owns products [r*PER, r*PER + PER): one search, then walk
     int cols[PER];
+    {
+        const int p0 = r * PER;
+        int t = 0, tb = 0, te = 0;
+        const int* bc = nullptr;
+        if (p0 < u) {
+            t = search_pre(m_pre, nA, p0);
+            tb = m_pre[t];
+            te = m_pre[t + 1];
+            bc = m_bc[t];
+        }
 #pragma unroll
-    for (int s = 0; s < PER; ++s) {
-        const int p = s * TEAM + r;
-        cols[s] = -1;
-        if (p < u) {
-            const int t = search_pre(m_pre, nA, p);
-            cols[s] = __ldg(m_bc[t] + (p - m_pre[t]));
+        for (int s = 0; s < PER; ++s) {
+            const int p = p0 + s;
+            cols[s] = -1;
+            if (p < u) {
+                while (p >= te) {
+                    ++t;
+                    tb = te;
+                    te = m_pre[t + 1];
+                    bc = m_bc[t];
+                }
+                cols[s] = __ldg(bc + (p - tb));
+            }
         }
     }
     Team<TEAM>::sync();
@@ -172,7 +191,7 @@ __device__ __forceinline__ void sym_row(const RowArgs& a, int unit, char* sm) {
 }
 
 template <int TEAM, int PER>
-__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, 1) k_sym_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, (TEAM == 32 && PER <= 8) ? 2 : 1) k_sym_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -196,8 +215,9 @@ __global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, 1) k_sym_rows(RowArgs
 template <int CAP, typename T>
 struct NumLayout {
     static constexpr int MAXA = CAP / 2;
-    static constexpr int cnt = 0;                                      // int[CAP + 1]
-    static constexpr int skey = ((CAP + 1) * 4 + 15) & ~15;           // u64[CAP]
+    static constexpr int NBMAX = CAP >= 8192 ? CAP : 2 * CAP;         // most buckets
+    static constexpr int cnt = 0;                                      // int[NBMAX + 4]
+    static constexpr int skey = (NBMAX + 4) * 4;                       // u64[CAP]
     static constexpr int ocol = skey + 8 * CAP;                        // int[CAP]
     static constexpr int oval = ocol + 4 * CAP;                        // T[CAP]
     static constexpr int oinst = oval + (int)sizeof(T) * CAP;          // u8[CAP]
@@ -210,6 +230,7 @@ struct NumLayout {
     static constexpr int m_pre = m_a + (int)sizeof(T) * MAXA;          // int[MAXA + 1]
     static constexpr int m_inst = m_pre + 4 * (MAXA + 1);              // u8[MAXA]
     static_assert(m_inst + MAXA <= oinst, "meta does not fit its alias region");
+    static_assert(bytes <= 227 * 1024, "team layout exceeds shared memory");
 };
 
 template <int TEAM, int PER, typename T>
@@ -239,29 +260,53 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
         if (r == 0) atomicOr(a.status, kStatusInternal);
         return;
     }
-    const int NB = pow2ceil(u);
+    // NB = 2 pow2ceil(u) buckets: most products sit alone in their bucket
+    const int NB = min(2 * pow2ceil(u), L::NBMAX);
     Bucketer bk;
-    bk.init(G.ncols, NB);
-    for (int i = r; i <= NB; i += TEAM) cnt[i] = 0;
+    bk.init(G.ncols, G.ncols_inv, NB);
+    for (int i = 4 * r; i <= NB; i += 4 * TEAM) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
     Team<TEAM>::sync();
 
     // gather: all loads first, then the bucket counts
     int col[PER];
     T val[PER];
     int hb[PER];  // low 16 bits: slot in bucket; high bits: instance
+    {
+        const int p0 = r * PER;
+        int t = 0, tb = 0, te = 0, ti = 0;
+        const int* bc = nullptr;
+        const T* bvp = nullptr;
+        T av = T(1);
+        if (p0 < u) {
+            t = search_pre(m_pre, nA, p0);
+            tb = m_pre[t];
+            te = m_pre[t + 1];
+            bc = m_bc[t];
+            bvp = m_bv[t];
+            av = m_a[t];
+            ti = m_inst[t];
+        }
 #pragma unroll
-    for (int s = 0; s < PER; ++s) {
-        const int p = s * TEAM + r;
-        col[s] = -1;
-        val[s] = T(0);
-        hb[s] = 0;
-        if (p < u) {
-            const int t = search_pre(m_pre, nA, p);
-            const int j = p - m_pre[t];
-            col[s] = __ldg(m_bc[t] + j);
-            const T bv = __ldg(m_bv[t] + j);
-            val[s] = a.merge ? bv : mul_rn(m_a[t], bv);
-            hb[s] = (int)m_inst[t] << 16;
+        for (int s = 0; s < PER; ++s) {
+            const int p = p0 + s;
+            col[s] = -1;
+            val[s] = T(0);
+            hb[s] = 0;
+            if (p < u) {
+                while (p >= te) {
+                    ++t;
+                    tb = te;
+                    te = m_pre[t + 1];
+                    bc = m_bc[t];
+                    bvp = m_bv[t];
+                    av = m_a[t];
+                    ti = m_inst[t];
+                }
+                col[s] = __ldg(bc + (p - tb));
+                const T bv = __ldg(bvp + (p - tb));
+                val[s] = a.merge ? bv : mul_rn(av, bv);
+                hb[s] = ti << 16;
+            }
         }
     }
 #pragma unroll
@@ -269,39 +314,72 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
         if (col[s] >= 0) hb[s] |= atomicAdd(&cnt[bk(col[s])], 1);
     Team<TEAM>::sync();
 
-    // bucket starts: exclusive scan of cnt[0..NB)
+    // bucket starts: exclusive scan of cnt[0..NB), each thread a contiguous
+    // slice (16-byte accesses when the slice allows)
     {
         const int per = NB >= TEAM ? NB / TEAM : 1;
         const int beg = r * per;
         int loc = 0;
-        if (beg < NB)
-            for (int i = 0; i < per; ++i) loc += cnt[beg + i];
+        if (beg < NB) {
+            if ((per & 3) == 0) {
+                for (int i = 0; i < per; i += 4) {
+                    const int4 v = *reinterpret_cast<const int4*>(cnt + beg + i);
+                    loc += v.x + v.y + v.z + v.w;
+                }
+            } else {
+                for (int i = 0; i < per; ++i) loc += cnt[beg + i];
+            }
+        }
         int tot;
         int ex = Team<TEAM>::scan_excl(loc, &tot, scratch);
-        if (beg < NB)
-            for (int i = 0; i < per; ++i) {
-                const int c = cnt[beg + i];
-                cnt[beg + i] = ex;
-                ex += c;
+        if (beg < NB) {
+            if ((per & 3) == 0) {
+                for (int i = 0; i < per; i += 4) {
+                    int4 v = *reinterpret_cast<const int4*>(cnt + beg + i);
+                    int4 o;
+                    o.x = ex; ex += v.x;
+                    o.y = ex; ex += v.y;
+                    o.z = ex; ex += v.z;
+                    o.w = ex; ex += v.w;
+                    *reinterpret_cast<int4*>(cnt + beg + i) = o;
+                }
+            } else {
+                for (int i = 0; i < per; ++i) {
+                    const int c = cnt[beg + i];
+                    cnt[beg + i] = ex;
+                    ex += c;
+                }
             }
+        }
         if (r == 0) cnt[NB] = tot;
     }
     Team<TEAM>::sync();
 
-    // scatter the (column, p) keys into bucket order
+    // a product alone in its bucket goes straight to its place; the others
+    // scatter their (column, p) keys into bucket order
+    const bool multi = a.merge || G.inst_count > 1;
 #pragma unroll
     for (int s = 0; s < PER; ++s)
         if (col[s] >= 0) {
-            const unsigned p = (unsigned)(s * TEAM + r);
-            skey[cnt[bk(col[s])] + (hb[s] & 0xffff)] = ((unsigned long long)(unsigned)col[s] << 32) | p;
+            const int b = bk(col[s]);
+            const int lo = cnt[b];
+            if (cnt[b + 1] - lo == 1) {
+                ocol[lo] = col[s];
+                oval[lo] = val[s];
+                if (multi) oinst[lo] = (unsigned char)(hb[s] >> 16);
+                col[s] = -1;
+            } else {
+                const unsigned p = (unsigned)(r * PER + s);
+                skey[lo + (hb[s] & 0xffff)] = ((unsigned long long)(unsigned)col[s] << 32) | p;
+            }
         }
     Team<TEAM>::sync();
 
-    // rank inside the bucket -> position in (column, p) order
+    // rank inside a shared bucket -> position in (column, p) order
 #pragma unroll
     for (int s = 0; s < PER; ++s)
         if (col[s] >= 0) {
-            const unsigned p = (unsigned)(s * TEAM + r);
+            const unsigned p = (unsigned)(r * PER + s);
             const int b = bk(col[s]);
             const int lo = cnt[b], hi = cnt[b + 1];
             const unsigned long long key = ((unsigned long long)(unsigned)col[s] << 32) | p;
@@ -310,13 +388,12 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
             const int pos = lo + rank;
             ocol[pos] = col[s];
             oval[pos] = val[s];
-            oinst[pos] = (unsigned char)(hb[s] >> 16);
+            if (multi) oinst[pos] = (unsigned char)(hb[s] >> 16);
         }
     Team<TEAM>::sync();
 
     // one output entry per run of equal columns; add the run in p order,
     // each instance's products first, then the instance sums in order
-    const bool multi = a.merge || G.inst_count > 1;
     T* cval = reinterpret_cast<T*>(G.cval);
     int nout = 0;
     for (int q0 = 0; q0 < u; q0 += TEAM) {
@@ -329,7 +406,7 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
         if (head) {
             T sub = oval[q], acc = T(0);
             bool have = false;
-            int ci = oinst[q];
+            int ci = multi ? oinst[q] : 0;
             for (int e = q + 1; e < u && ocol[e] == c; ++e) {
                 const T v = oval[e];
                 if (multi && oinst[e] != ci) {
@@ -353,8 +430,329 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
     Team<TEAM>::sync();
 }
 
+// ------------------------------------------------- numeric, warp-team variant
+//
+// The same accumulator as num_row, arranged for SIMT efficiency:
+//   place     every product goes to its slot in its bucket (bucket start +
+//             arrival order); for a bucket of one product that slot is final
+//   sort      only buckets holding several products are sorted in place by
+//             (column, p), one bucket per lane, from a compacted work list
+//   compact   run heads found with shuffles; a head whose successor has
+//             another column takes its value as is, otherwise adds its run
+// The meta keeps B-row offsets instead of pointers (instance base pointers
+// are looked up when the instance changes).
+
+template <int CAP, typename T>
+struct WNumLayout {
+    static constexpr int MAXA = CAP / 2;
+    static constexpr int NBMAX = 2 * CAP;
+    static constexpr int cnt = 0;                                  // int[NBMAX + 4]
+    static constexpr int ocol = (NBMAX + 4) * 4;                   // int[CAP]
+    static constexpr int oval = ocol + 4 * CAP;                    // T[CAP]
+    static constexpr int op = oval + (int)sizeof(T) * CAP;         // u16[CAP] product index
+    static constexpr int oinst = op + 2 * CAP;                     // u8[CAP]
+    static constexpr int wl = (oinst + CAP + 3) & ~3;              // u16[CAP / 2] buckets to sort
+    static constexpr int bytes = (wl + CAP + 15) & ~15;
+    // meta, aliased over [ocol, wl) while the products are gathered
+    static constexpr int m_pre = ocol;                             // int[MAXA + 1]
+    static constexpr int m_bs = m_pre + 4 * (MAXA + 1);            // int[MAXA]
+    static constexpr int m_a = (m_bs + 4 * MAXA + 7) & ~7;         // T[MAXA]
+    static constexpr int m_inst = m_a + (int)sizeof(T) * MAXA;     // u8[MAXA]
+    static_assert(m_inst + MAXA <= wl, "meta does not fit its alias region");
+    static_assert((oval & 7) == 0, "value array alignment");
+};
+
+template <int PER, typename T>
+__device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm) {
+    constexpr int CAP = 32 * PER;
+    using L = WNumLayout<CAP, T>;
+    int* cnt = reinterpret_cast<int*>(sm + L::cnt);
+    int* ocol = reinterpret_cast<int*>(sm + L::ocol);
+    T* oval = reinterpret_cast<T*>(sm + L::oval);
+    unsigned short* op = reinterpret_cast<unsigned short*>(sm + L::op);
+    unsigned char* oinst = reinterpret_cast<unsigned char*>(sm + L::oinst);
+    unsigned short* wl = reinterpret_cast<unsigned short*>(sm + L::wl);
+    int* m_pre = reinterpret_cast<int*>(sm + L::m_pre);
+    int* m_bs = reinterpret_cast<int*>(sm + L::m_bs);
+    T* m_a = reinterpret_cast<T*>(sm + L::m_a);
+    unsigned char* m_inst = reinterpret_cast<unsigned char*>(sm + L::m_inst);
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int g = unit_group(a.unit_base, a.ngroups, unit);
+    const GroupDev& G = a.groups[g];
+    const int rho = (int)(unit - a.unit_base[g]);
+    const int row_begin = __ldg(G.crp + rho);
+    const int row_len = __ldg(G.crp + rho + 1) - row_begin;
+    const int ncols = G.ncols;
+    const unsigned long long ncols_inv = G.ncols_inv;
+    const int ib = G.inst_begin, icount = G.inst_count;
+    const bool multi = a.merge || icount > 1;
+
+    // ---- meta: B-row offset, a_ik, instance and prefix per A entry
+    int nA = 0, u = 0;
+    for (int t = 0; t < icount; ++t) {
+        const InstDev& I = a.inst[ib + t];
+        int a0 = 0, a1 = 1;
+        if (!a.merge) {
+            a0 = __ldg(I.arp + rho);
+            a1 = __ldg(I.arp + rho + 1);
+        }
+        for (int e0 = a0; e0 < a1; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < a1;
+            int len = 0, bs = 0;
+            T av = T(1);
+            if (valid) {
+                const int k = a.merge ? rho : __ldg(I.acol + e);
+                bs = __ldg(I.brp + k);
+                len = __ldg(I.brp + k + 1) - bs;
+                if (!a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
+            }
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int idx = nA + lane;
+            if (valid && idx < L::MAXA) {
+                m_pre[idx] = u + x - len;
+                m_bs[idx] = bs;
+                m_a[idx] = av;
+                m_inst[idx] = (unsigned char)t;
+            }
+            nA += min(32, a1 - e0);
+            u += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    if (nA > L::MAXA || u > CAP) {
+        if (lane == 0) atomicOr(a.status, kStatusInternal);
+        __syncwarp();
+        return;
+    }
+    if (lane == 0) m_pre[nA] = u;
+    const int NB = 2 * pow2ceil(u);
+    Bucketer bk;
+    bk.init(ncols, ncols_inv, NB);
+    for (int i = 4 * lane; i <= NB; i += 128) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
+    // a row whose nnz equals its product count has no repeated column: it
+    // only needs sorting (no tie-break, no run compaction)
+    const bool distinct = row_len == u;
+    __syncwarp();
+
+    // ---- gather: lane owns products [lane*PER, lane*PER + PER)
+    int col[PER];
+    T val[PER];
+    int hh[PER];  // slot in bucket (low 16 bits) | instance << 16
+    {
+        const int p0 = lane * PER;
+        int t = 0, tb = 0, te = 0, ti = -1, bs = 0;
+        const int* bcol = nullptr;
+        const T* bval = nullptr;
+        T av = T(1);
+        if (p0 < u) {
+            int lo = 0, hi = nA;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (m_pre[mid] <= p0) lo = mid; else hi = mid;
+            }
+            t = lo;
+            tb = m_pre[t];
+            te = m_pre[t + 1];
+            bs = m_bs[t];
+            av = m_a[t];
+            ti = m_inst[t];
+            bcol = a.inst[ib + ti].bcol;
+            bval = reinterpret_cast<const T*>(a.inst[ib + ti].bval);
+        }
+#pragma unroll
+        for (int s = 0; s < PER; ++s) {
+            const int p = p0 + s;
+            col[s] = -1;
+            val[s] = T(0);
+            hh[s] = 0;
+            if (p < u) {
+                while (p >= te) {
+                    ++t;
+                    tb = te;
+                    te = m_pre[t + 1];
+                    bs = m_bs[t];
+                    av = m_a[t];
+                    const int tn = m_inst[t];
+                    if (tn != ti) {
+                        ti = tn;
+                        bcol = a.inst[ib + ti].bcol;
+                        bval = reinterpret_cast<const T*>(a.inst[ib + ti].bval);
+                    }
+                }
+                const int f = bs + (p - tb);
+                col[s] = __ldg(bcol + f);
+                const T bv = __ldg(bval + f);
+                val[s] = a.merge ? bv : mul_rn(av, bv);
+                hh[s] = ti << 16;
+            }
+        }
+    }
+    // bucket counts; the second arrival in a bucket lists it for sorting
+    int nwl = 0;
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        int h = -1, b = 0;
+        if (col[s] >= 0) {
+            b = bk(col[s]);
+            h = atomicAdd(&cnt[b], 1);
+            hh[s] |= h;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, h == 1);
+        if (h == 1) wl[nwl + __popc(m & lt)] = (unsigned short)b;
+        nwl += __popc(m);
+    }
+    __syncwarp();
+
+    // ---- bucket starts: exclusive scan in rounds of 32 x 4 counters
+    {
+        int base = 0;
+        for (int i0 = 0; i0 < NB; i0 += 128) {
+            const int i = i0 + 4 * lane;
+            int4 v = make_int4(0, 0, 0, 0);
+            if (i < NB) v = *reinterpret_cast<const int4*>(cnt + i);
+            const int loc = v.x + v.y + v.z + v.w;
+            int x = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            int ex = base + x - loc;
+            if (i < NB) {
+                int4 o;
+                o.x = ex; ex += v.x;
+                o.y = ex; ex += v.y;
+                o.z = ex; ex += v.z;
+                o.w = ex;
+                *reinterpret_cast<int4*>(cnt + i) = o;
+            }
+            base += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) cnt[NB] = u;
+    }
+    __syncwarp();
+
+    // ---- place every product at its bucket slot
+#pragma unroll
+    for (int s = 0; s < PER; ++s)
+        if (col[s] >= 0) {
+            const int pos = cnt[bk(col[s])] + (hh[s] & 0xffff);
+            ocol[pos] = col[s];
+            oval[pos] = val[s];
+            if (!distinct) {
+                op[pos] = (unsigned short)(lane * PER + s);
+                if (multi) oinst[pos] = (unsigned char)(hh[s] >> 16);
+            }
+        }
+    __syncwarp();
+
+    // ---- sort each listed bucket in place: by column, ties by p
+    for (int w = lane; w < nwl; w += 32) {
+        const int b = wl[w];
+        const int lo = cnt[b], hi = cnt[b + 1];
+        if (distinct) {
+            for (int i = lo + 1; i < hi; ++i) {
+                const int c = ocol[i];
+                const T v = oval[i];
+                int j = i - 1;
+                while (j >= lo && ocol[j] > c) {
+                    ocol[j + 1] = ocol[j];
+                    oval[j + 1] = oval[j];
+                    --j;
+                }
+                ocol[j + 1] = c;
+                oval[j + 1] = v;
+            }
+        } else {
+            for (int i = lo + 1; i < hi; ++i) {
+                const int c = ocol[i];
+                const int pp = op[i];
+                const T v = oval[i];
+                const unsigned char ins = multi ? oinst[i] : 0;
+                int j = i - 1;
+                while (j >= lo && (ocol[j] > c || (ocol[j] == c && op[j] > pp))) {
+                    ocol[j + 1] = ocol[j];
+                    op[j + 1] = op[j];
+                    oval[j + 1] = oval[j];
+                    if (multi) oinst[j + 1] = oinst[j];
+                    --j;
+                }
+                ocol[j + 1] = c;
+                op[j + 1] = (unsigned short)pp;
+                oval[j + 1] = v;
+                if (multi) oinst[j + 1] = ins;
+            }
+        }
+    }
+    __syncwarp();
+
+    T* cval = reinterpret_cast<T*>(G.cval) + row_begin;
+    int* ccol = G.ccol + row_begin;
+    if (distinct) {
+        // ---- sorted products are the row: copy out
+        for (int q = lane; q < u; q += 32) {
+            ccol[q] = ocol[q];
+            cval[q] = oval[q];
+        }
+        __syncwarp();
+        return;
+    }
+
+    // ---- compact runs of equal columns and write the row
+    int nout = 0, carry = -1;
+    for (int q0 = 0; q0 < u; q0 += 32) {
+        const int q = q0 + lane;
+        const bool valid = q < u;
+        const int c = valid ? ocol[q] : -2;
+        int prev = __shfl_up_sync(0xffffffffu, c, 1);
+        if (lane == 0) prev = carry;
+        int next = __shfl_down_sync(0xffffffffu, c, 1);
+        if (lane == 31) next = q + 1 < u ? ocol[q + 1] : -2;
+        const bool head = valid && c != prev;
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (head) {
+            T res = oval[q];
+            if (next == c) {
+                // several products on this column: add them in p order (in
+                // merge or multi-instance mode each instance's products first)
+                T sub = res, acc = T(0);
+                bool have = false;
+                int ci = multi ? oinst[q] : 0;
+                for (int e = q + 1; e < u && ocol[e] == c; ++e) {
+                    const T v = oval[e];
+                    if (multi && oinst[e] != ci) {
+                        acc = have ? add_rn(acc, sub) : sub;
+                        have = true;
+                        sub = v;
+                        ci = oinst[e];
+                    } else {
+                        sub = add_rn(sub, v);
+                    }
+                }
+                res = have ? add_rn(acc, sub) : sub;
+            }
+            const int idx = nout + __popc(hm & lt);
+            if (idx < row_len) {
+                ccol[idx] = c;
+                cval[idx] = res;
+            }
+        }
+        nout += __popc(hm);
+        carry = __shfl_sync(0xffffffffu, c, 31);
+    }
+    if (lane == 0 && nout != row_len) atomicOr(a.status, kStatusInternal);
+    __syncwarp();
+}
+
 template <int TEAM, int PER, typename T>
-__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, 1) k_num_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, (TEAM == 32 && PER <= 8) ? 2 : 1) k_num_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -364,13 +762,17 @@ __global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, 1) k_num_rows(RowArgs
         const int w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
         team = blockIdx.x * wpb + w;
         nteams = gridDim.x * wpb;
-        sm = smem + w * NumLayout<CAP, T>::bytes;
+        sm = smem + w * WNumLayout<CAP, T>::bytes;
     } else {
         team = blockIdx.x;
         nteams = gridDim.x;
         sm = smem;
     }
-    for (int i = begin + team; i < end; i += nteams) num_row<TEAM, PER, T>(a, __ldg(a.list + i), sm);
+    if constexpr (TEAM == 32) {
+        for (int i = begin + team; i < end; i += nteams) num_row_warp<PER, T>(a, __ldg(a.list + i), sm);
+    } else {
+        for (int i = begin + team; i < end; i += nteams) num_row<TEAM, PER, T>(a, __ldg(a.list + i), sm);
+    }
 }
 
 // ---------------------------------------------------------------- heavy rows

@@ -9,7 +9,7 @@ static int num_smem_bytes_t(int variant, int wpb) {
     int bytes = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        bytes = NumLayout<SS::CAP, T>::bytes * (SS::TEAM == 32 ? wpb : 1);
+        bytes = SS::TEAM == 32 ? WNumLayout<SS::CAP, T>::bytes * wpb : NumLayout<SS::CAP, T>::bytes;
         return cudaSuccess;
     });
     return bytes;
