@@ -200,6 +200,43 @@ spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst
                              const int32_t* group_ptr, spgemm_csr_out* C, int64_t* c_nnz,
                              const spgemm_tune* tune, spgemm_stream_t stream);
 
+/* ------------------------------------------ trident partition (Sec. 3.2)
+ *
+ * spgemm_tile_split: cut X into nrp x ncp tiles.  Tile (rp, cp) holds rows
+ * [row_bounds[rp], row_bounds[rp+1]) and columns [col_bounds[cp],
+ * col_bounds[cp+1]) of X, with columns re-based to the tile (j -> j -
+ * col_bounds[cp]) and each row's entries in X's stored order.  row_bounds
+ * (nrp+1) and col_bounds (ncp+1) are host arrays, non-decreasing, from 0 to
+ * X.nrows / X.ncols; 1 <= nrp, ncp and ncp <= 64.  tiles[rp * ncp + cp]
+ * describes tile (rp, cp): nrows/ncols must equal the bound differences.
+ * Sizing call: tile_nnz != NULL -> writes every tile's row_ptr and
+ * tile_nnz[rp * ncp + cp] (host), synchronising once.  Fill call: tile_nnz
+ * == NULL -> writes col_idx / val of every tile (val skipped when X.val is
+ * NULL), asynchronous.
+ * The trident split of A (m x kk) for a grid q x q x lambda uses row bounds
+ * (coarse tile t) floor(t m / q) refined into lambda slices
+ * lo + floor(s (hi - lo) / lambda), and column bounds floor(t kk / q); the
+ * split of B uses coarse bounds on both sides.
+ */
+spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X, int32_t nrp,
+                                const int32_t* row_bounds, int32_t ncp, const int32_t* col_bounds,
+                                spgemm_csr_out* tiles, int64_t* tile_nnz, spgemm_stream_t stream);
+
+/* ------------------------------------ static-Cannon rounds (Alg. 1, Eq. 2)
+ *
+ * spgemm_trident_schedule: the instance list of the trident grid q x q x
+ * lambda in the layout spgemm_batched takes.  Output block (i, j, k) is group
+ * g = (i q + j) lambda + k; its q instances are the rounds r = 0..q-1 in
+ * order, round r multiplying A slice (i, r', k) by B tile (r', j) with the
+ * stagger r' = (r + i + j) mod q.  a_tile[t] = (i lambda + k) q + r' indexes
+ * the tiles of spgemm_tile_split on A (row slices x column tiles) and
+ * b_tile[t] = r' q + j those of B; group_ptr[g] = g q.  Host arrays of
+ * q*q*lambda*q (a_tile, b_tile) and q*q*lambda + 1 (group_ptr) entries.
+ * Host-only: needs no handle and no device.
+ */
+spgemm_status spgemm_trident_schedule(int32_t q, int32_t lambda, int32_t* a_tile, int32_t* b_tile,
+                                      int32_t* group_ptr);
+
 /* --------------------------------------------------------- instrumentation */
 
 /* Number of kernels this handle has launched since creation (host counter). */

@@ -65,6 +65,10 @@ SIGNATURES = {
     "spgemm_merge": ([P, ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),
     "spgemm_batched": ([P, ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), I32,
                         ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, ctypes.POINTER(Tune), P], ctypes.c_int),
+    "spgemm_tile_split": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), I32, ctypes.POINTER(I32), I32,
+                           ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),
+    "spgemm_trident_schedule": ([I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
+                                ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

@@ -266,3 +266,102 @@ class BatchPlan:
 def batched(As, Bs, group_ptr=None, handle: Handle | None = None, tune: Tune | None = None, stream=None):
     """Outputs C[g] = sum over the group's instances (in order) of A[t] B[t]."""
     return BatchPlan(As, Bs, group_ptr).run(handle, tune, stream)
+
+
+# ------------------------------------------------------ trident partition
+
+def trident_bounds(n: int, q: int, lam: int = 1):
+    """(coarse, fine) boundaries of the hybrid 2D + 1D split of [0, n) (paper
+    Sec. 3.2): coarse tile t is [floor(t n / q), floor((t+1) n / q)); each is
+    cut into lam contiguous slices lo + floor(s (hi - lo) / lam)."""
+    coarse = [(t * n) // q for t in range(q + 1)]
+    fine = [coarse[t] + (s * (coarse[t + 1] - coarse[t])) // lam for t in range(q) for s in range(lam)] + [n]
+    return coarse, fine
+
+
+def tile_split(X: DeviceCSR, row_bounds, col_bounds, handle: Handle | None = None, stream=None):
+    """Cut X into tiles[rp][cp] on the device (columns re-based to the tile)."""
+    h = handle or default_handle()
+    nrp, ncp = len(row_bounds) - 1, len(col_bounds) - 1
+    rb = (ctypes.c_int32 * (nrp + 1))(*row_bounds)
+    cb = (ctypes.c_int32 * (ncp + 1))(*col_bounds)
+    dev = X.row_ptr.device
+    dt = X.val.dtype if X.val is not None else torch.float64
+    tiles = [[DeviceCSR(row_bounds[r + 1] - row_bounds[r], col_bounds[c + 1] - col_bounds[c],
+                        torch.empty(row_bounds[r + 1] - row_bounds[r] + 1, dtype=torch.int32, device=dev),
+                        torch.empty(0, dtype=torch.int32, device=dev), None)
+              for c in range(ncp)] for r in range(nrp)]
+    outs = (CsrOut * (nrp * ncp))()
+    for r in range(nrp):
+        for c in range(ncp):
+            T = tiles[r][c]
+            outs[r * ncp + c] = CsrOut(T.nrows, T.ncols, T.row_ptr.data_ptr(), None, None)
+    nnz = (ctypes.c_int64 * (nrp * ncp))()
+    xin = X.as_in()
+    check(_abi.lib().spgemm_tile_split(h.ptr, _dtype_code(dt), ctypes.byref(xin), nrp, rb, ncp, cb, outs, nnz,
+                                       _stream(stream)), "spgemm_tile_split(size)")
+    for r in range(nrp):
+        for c in range(ncp):
+            T = tiles[r][c]
+            n = int(nnz[r * ncp + c])
+            T.col = torch.empty(n, dtype=torch.int32, device=dev)
+            T.val = torch.empty(n, dtype=dt, device=dev) if X.val is not None else None
+            outs[r * ncp + c] = T.as_out()
+    check(_abi.lib().spgemm_tile_split(h.ptr, _dtype_code(dt), ctypes.byref(xin), nrp, rb, ncp, cb, outs, None,
+                                       _stream(stream)), "spgemm_tile_split(fill)")
+    return tiles
+
+
+def trident_schedule(q: int, lam: int):
+    """Instances of the static-Cannon rounds (Alg. 1, Eq. 2) from the library:
+    (a_tile, b_tile, group_ptr)."""
+    n = q * q * lam * q
+    a = (ctypes.c_int32 * n)()
+    b = (ctypes.c_int32 * n)()
+    gp = (ctypes.c_int32 * (q * q * lam + 1))()
+    check(_abi.lib().spgemm_trident_schedule(q, lam, a, b, gp), "spgemm_trident_schedule")
+    return list(a), list(b), list(gp)
+
+
+class TridentPlan:
+    """The trident grid q x q x lambda of C = A B on one device.
+
+    The partition (Sec. 3.2) runs on the device; the rounds of every output
+    block follow the static-Cannon stagger (Alg. 1, Eq. 2); each round's
+    partial A_{i r' k} B_{r' j} uses the whole tile B_{r' j} (the allgather of
+    Alg. 2 is the tile itself on one device).
+
+    mode "fused": one batched call, each output row accumulates its q rounds
+    at once (partials never materialised).  mode "unfused": every partial is
+    a separate instance written to memory, then each block is the ordered sum
+    of its partials (the paper's spgeam step).  Both give identical bits.
+    """
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, q: int, lam: int, handle: Handle | None = None):
+        self.q, self.lam = q, lam
+        self.h = handle or default_handle()
+        _, rows_fine = trident_bounds(A.nrows, q, lam)
+        kc, _ = trident_bounds(A.ncols, q, 1)
+        nc, _ = trident_bounds(B.ncols, q, 1)
+        self.row_bounds, self.k_bounds, self.col_bounds = rows_fine, kc, nc
+        self.A_tiles = tile_split(A, rows_fine, kc, self.h)   # [i*lam + k][r]
+        self.B_tiles = tile_split(B, kc, nc, self.h)          # [r][j]
+        a_t, b_t, gp = trident_schedule(q, lam)
+        self.As = [self.A_tiles[t // q][t % q] for t in a_t]
+        self.Bs = [self.B_tiles[t // q][t % q] for t in b_t]
+        self.group_ptr = gp
+        self.fused = BatchPlan(self.As, self.Bs, gp)
+        self.partials = None
+
+    def block_index(self, i: int, j: int, k: int) -> int:
+        return (i * self.q + j) * self.lam + k
+
+    def run_fused(self, tune: Tune | None = None, stream=None):
+        return self.fused.run(self.h, tune, stream)
+
+    def run_unfused(self, tune: Tune | None = None, stream=None):
+        if self.partials is None:
+            self.partials = BatchPlan(self.As, self.Bs)
+        P = self.partials.run(self.h, tune, stream)
+        return [merge(P[self.group_ptr[g]:self.group_ptr[g + 1]], self.h, stream)
+                for g in range(len(self.group_ptr) - 1)]

@@ -648,6 +648,129 @@ spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst
     return run(h, dtype, false, inst, groups, sizing, c_nnz, tn, checks, reinterpret_cast<cudaStream_t>(stream));
 }
 
+spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X, int32_t nrp,
+                                const int32_t* row_bounds, int32_t ncp, const int32_t* col_bounds,
+                                spgemm_csr_out* tiles, int64_t* tile_nnz, spgemm_stream_t stream) {
+    if (!h || !X || !csr_in_ok(X, false) || !row_bounds || !col_bounds || !tiles) return SPGEMM_ERR_INVALID_ARG;
+    if (nrp < 1 || ncp < 1 || ncp > 64) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (row_bounds[0] != 0 || row_bounds[nrp] != X->nrows || col_bounds[0] != 0 || col_bounds[ncp] != X->ncols)
+        return SPGEMM_ERR_SHAPE;
+    for (int i = 0; i < nrp; ++i)
+        if (row_bounds[i + 1] < row_bounds[i]) return SPGEMM_ERR_INVALID_ARG;
+    for (int i = 0; i < ncp; ++i)
+        if (col_bounds[i + 1] < col_bounds[i]) return SPGEMM_ERR_INVALID_ARG;
+    const bool sizing = tile_nnz != nullptr;
+    const int nt = nrp * ncp;
+    std::vector<GroupDev> groups(nt);  // indexed by tile (rp, cp)
+    for (int rp = 0; rp < nrp; ++rp)
+        for (int cp = 0; cp < ncp; ++cp) {
+            const spgemm_csr_out& T = tiles[rp * ncp + cp];
+            if (!T.row_ptr) return SPGEMM_ERR_INVALID_ARG;
+            if (T.nrows != row_bounds[rp + 1] - row_bounds[rp] || T.ncols != col_bounds[cp + 1] - col_bounds[cp])
+                return SPGEMM_ERR_SHAPE;
+            groups[rp * ncp + cp] = {0, 1, T.nrows, T.ncols, T.row_ptr, T.col_idx, T.val, 0};
+        }
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    h->plan_valid = false;
+    const long long m = X->nrows;
+    const long long U = m * ncp;
+    if (U >= (1ll << 31) - 1) return SPGEMM_ERR_UNSUPPORTED;
+    // scan order: units (cp, row); group order (cp, rp)
+    std::vector<GroupDev> sgroups(nt);
+    std::vector<long long> ubase(nt + 1);
+    for (int cp = 0; cp < ncp; ++cp)
+        for (int rp = 0; rp < nrp; ++rp) {
+            sgroups[cp * nrp + rp] = groups[rp * ncp + cp];
+            ubase[cp * nrp + rp] = cp * m + row_bounds[rp];
+        }
+    ubase[nt] = U;
+    if (m == 0) {
+        if (sizing) {
+            for (int t = 0; t < nt; ++t) {
+                TSG_CHECK(cudaMemsetAsync(groups[t].crp, 0, sizeof(int), st));
+                tile_nnz[t] = 0;
+            }
+        }
+        return SPGEMM_OK;
+    }
+    if (U > h->units_cap) {
+        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1));
+        TSG_TRY(grow(h->units, bytes));
+        h->units_cap = U;
+    }
+    char* ub = static_cast<char*>(h->units.p);
+    int* d_counts = reinterpret_cast<int*>(ub + align16(h->units_cap) + align16(4 * h->units_cap));
+    long long* d_ex = reinterpret_cast<long long*>(ub + align16(h->units_cap) + 2 * align16(4 * h->units_cap));
+    const long long nblk = scan_blocks(U);
+    size_t o_bsum = 0;
+    size_t o_nnz = o_bsum + align16(8 * nblk);
+    size_t o_ubase = o_nnz + align16(8 * nt);
+    size_t o_sg = o_ubase + align16(8 * (nt + 1));
+    size_t o_tg = o_sg + align16(sizeof(GroupDev) * nt);
+    size_t o_rb = o_tg + align16(sizeof(GroupDev) * nt);
+    size_t o_cb = o_rb + align16(4 * (nrp + 1));
+    size_t bytes = o_cb + align16(4 * (ncp + 1));
+    TSG_TRY(grow(h->small, bytes));
+    char* sb = static_cast<char*>(h->small.p);
+    std::vector<char> stage(bytes - o_ubase);
+    std::memcpy(stage.data(), ubase.data(), 8 * (nt + 1));
+    std::memcpy(stage.data() + (o_sg - o_ubase), sgroups.data(), sizeof(GroupDev) * nt);
+    std::memcpy(stage.data() + (o_tg - o_ubase), groups.data(), sizeof(GroupDev) * nt);
+    std::memcpy(stage.data() + (o_rb - o_ubase), row_bounds, 4 * (nrp + 1));
+    std::memcpy(stage.data() + (o_cb - o_ubase), col_bounds, 4 * (ncp + 1));
+    TSG_CHECK(cudaMemcpyAsync(sb + o_ubase, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
+    const int* d_rb = reinterpret_cast<const int*>(sb + o_rb);
+    const int* d_cb = reinterpret_cast<const int*>(sb + o_cb);
+    PhaseScope ps(h, 5, st);
+    if (sizing) {
+        for (int t = 0; t < nt; ++t)
+            if (groups[t].nrows == 0) TSG_CHECK(cudaMemsetAsync(groups[t].crp, 0, sizeof(int), st));
+        long long* d_nnz = reinterpret_cast<long long*>(sb + o_nnz);
+        TSG_CHECK(cudaMemsetAsync(d_nnz, 0, 8 * nt, st));
+        TSG_CHECK(launch_split_count(X->row_ptr, X->col_idx, X->nrows, d_cb, ncp, d_counts, st));
+        TSG_CHECK(launch_scan(d_counts, U, reinterpret_cast<long long*>(sb + o_bsum), d_ex, st));
+        TSG_CHECK(launch_rowptr(reinterpret_cast<const GroupDev*>(sb + o_sg), reinterpret_cast<const long long*>(sb + o_ubase),
+                                nt, U, d_ex, d_nnz, st));
+        h->launches += 5;
+        TSG_TRY(grow_pinned(h, 8 * nt));
+        long long* p_nnz = static_cast<long long*>(h->pinned);
+        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8 * nt, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        for (int cp = 0; cp < ncp; ++cp)
+            for (int rp = 0; rp < nrp; ++rp) tile_nnz[rp * ncp + cp] = p_nnz[cp * nrp + rp];
+        return SPGEMM_OK;
+    }
+    TSG_CHECK(launch_split_fill(dtype, X->row_ptr, X->col_idx, X->val, X->nrows, d_rb, nrp, d_cb, ncp,
+                                reinterpret_cast<const GroupDev*>(sb + o_tg), st));
+    ++h->launches;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_trident_schedule(int32_t q, int32_t lambda, int32_t* a_tile, int32_t* b_tile,
+                                      int32_t* group_ptr) {
+    if (q < 1 || lambda < 1 || !a_tile || !b_tile || !group_ptr) return SPGEMM_ERR_INVALID_ARG;
+    if ((long long)q * q * lambda * q > (1 << 20)) return SPGEMM_ERR_INVALID_ARG;
+    int t = 0, g = 0;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j)
+            for (int k = 0; k < lambda; ++k) {
+                group_ptr[g++] = t;
+                for (int r = 0; r < q; ++r) {
+                    const int rr = (r + i + j) % q;
+                    a_tile[t] = (i * lambda + k) * q + rr;
+                    b_tile[t] = rr * q + j;
+                    ++t;
+                }
+            }
+    group_ptr[g] = t;
+    return SPGEMM_OK;
+}
+
 spgemm_status spgemm_launch_count(const spgemm_handle* h, int64_t* count) {
     if (!h || !count) return SPGEMM_ERR_INVALID_ARG;
     *count = h->launches;

@@ -64,4 +64,10 @@ cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& a, void* dense, int
                              cudaStream_t s);
 int heavy_chunk_for(int ncols);
 
+// trident partition (partition.cu)
+cudaError_t launch_split_count(const int* rp, const int* col, int nrows, const int* cb, int ncp, int* counts,
+                               cudaStream_t s);
+cudaError_t launch_split_fill(int dtype, const int* rp, const int* col, const void* val, int nrows, const int* rb,
+                              int nrp, const int* cb, int ncp, const GroupDev* tiles, cudaStream_t s);
+
 }  // namespace tsg

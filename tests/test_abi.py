@@ -76,3 +76,26 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_abi, "_lib", None)
     with pytest.raises(RuntimeError, match="CUDA library missing"):
         _abi.lib()
+
+
+def test_trident_schedule_matches_static_cannon(lib):
+    import oracle
+    from paper_2603_21444_gb300 import api
+    for q, lam in [(1, 1), (2, 2), (3, 2), (4, 4), (5, 3)]:
+        a, b, gp = api.trident_schedule(q, lam)
+        assert gp == [g * q for g in range(q * q * lam + 1)]
+        for i in range(q):
+            for j in range(q):
+                for k in range(lam):
+                    g = (i * q + j) * lam + k
+                    rounds = oracle.static_cannon_schedule(q, i, j)
+                    for r, rr in enumerate(rounds):
+                        assert a[gp[g] + r] == (i * lam + k) * q + rr
+                        assert b[gp[g] + r] == rr * q + j
+
+
+def test_trident_bounds_match_oracle():
+    import oracle
+    from paper_2603_21444_gb300 import api
+    for n, q, lam in [(64, 2, 2), (97, 3, 2), (2 ** 21, 4, 4), (10, 4, 3), (5, 1, 1)]:
+        assert api.trident_bounds(n, q, lam) == tuple(oracle.trident_bounds(n, q, lam))

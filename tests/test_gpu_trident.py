@@ -107,3 +107,34 @@ def test_batched_with_empty_group_rows(tsg, handle):
     assert host(Cs[0])[0].tolist() == [0]
     same(Cs[1], oracle.spgemm(a1, b0)[0])
     assert host(Cs[2])[0].tolist() == [0] * 6
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_tile_split_matches_oracle_submatrix(tsg, handle, dtype):
+    X = gen.er_variable(1000, 900, 40, 77, dtype, "normal", p_empty=0.1)
+    dX = tsg.DeviceCSR.from_host(X)
+    _, rb = oracle.trident_bounds(X.nrows, 3, 2)
+    cb, _ = oracle.trident_bounds(X.ncols, 5, 1)
+    tiles = tsg.tile_split(dX, rb, cb, handle)
+    torch.cuda.synchronize()
+    for r in range(len(rb) - 1):
+        for c in range(len(cb) - 1):
+            same(tiles[r][c], oracle.submatrix(X, rb[r], rb[r + 1], cb[c], cb[c + 1]))
+
+
+@pytest.mark.parametrize("q,lam", [(4, 4), (3, 2), (1, 1)])
+def test_trident_plan_fused_and_unfused(tsg, handle, q, lam):
+    n, d = 1 << 12, 32
+    A = gen.er(n, n, d, 4, np.float64, "uniform")
+    B = gen.er(n, n, d, 5, np.float64, "uniform")
+    ref, _ = oracle.trident_product(A, B, q, lam)
+    plan = tsg.TridentPlan(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), q, lam, handle)
+    fused = plan.run_fused()
+    unfused = plan.run_unfused()
+    torch.cuda.synchronize()
+    for i in range(q):
+        for j in range(q):
+            for k in range(lam):
+                g = plan.block_index(i, j, k)
+                same(fused[g], ref[i][j][k])
+                same(unfused[g], ref[i][j][k])
