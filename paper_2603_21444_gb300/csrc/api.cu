@@ -51,6 +51,7 @@ struct spgemm_handle {
     long long units_cap = -1;
     DevBuf small;
     DevBuf dense;
+    DevBuf status;  // the device status word latched by kernels
     void* pinned = nullptr;
     size_t pinned_n = 0;
     // plan cache (bin lists of the last sizing call)
@@ -292,7 +293,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     int* d_hist = reinterpret_cast<int*>(sb + o_hist);
     int* d_off = reinterpret_cast<int*>(sb + o_off);
     int* d_cur = reinterpret_cast<int*>(sb + o_cur);
-    unsigned* d_status = reinterpret_cast<unsigned*>(sb + o_status);
+    TSG_TRY(grow(h->status, 16, st, true));
+    unsigned* d_status = static_cast<unsigned*>(h->status.p);
     long long* d_bsum = reinterpret_cast<long long*>(sb + o_bsum);
     long long* d_nnz = reinterpret_cast<long long*>(sb + o_nnz);
     long long* d_ubase = reinterpret_cast<long long*>(sb + o_ubase);
@@ -314,8 +316,6 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         std::memcpy(stage.data() + (o_groups - o_ubase), groups.data(), sizeof(GroupDev) * ngroups);
         TSG_CHECK(cudaMemcpyAsync(sb + o_ubase, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
     }
-    TSG_CHECK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
-
     // ---- plan signature (input patterns, output row_ptr, bins)
     uint64_t sig = 1469598103934665603ull;
     sig = fnv(sig, &merge, sizeof(merge));
@@ -341,6 +341,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         TSG_CHECK(cudaStreamSynchronize(st));
         if (*p_status & kStatusNotCanonical) {
             h->plan_valid = false;
+            TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
             return SPGEMM_ERR_NOT_CANONICAL;
         }
     }
@@ -410,6 +411,9 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         const unsigned status = *p_status;
+        // a latched error (this call's or an earlier asynchronous call's) is
+        // reported once, then cleared
+        if (status) TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
         if (status & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
         if (status & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;
         if (status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
@@ -461,8 +465,10 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     if (tune.validate) {
         TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
         TSG_CHECK(cudaStreamSynchronize(st));
-        if (*p_status & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
-        if (*p_status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+        const unsigned status = *p_status;
+        if (status) TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
+        if (status & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
+        if (status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
     }
     return SPGEMM_OK;
 }
@@ -538,6 +544,7 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->units.p) cudaFree(h->units.p);
     if (h->small.p) cudaFree(h->small.p);
     if (h->dense.p) cudaFree(h->dense.p);
+    if (h->status.p) cudaFree(h->status.p);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -779,12 +786,11 @@ spgemm_status spgemm_launch_count(const spgemm_handle* h, int64_t* count) {
 
 spgemm_status spgemm_device_status(spgemm_handle* h) {
     if (!h) return SPGEMM_ERR_INVALID_ARG;
-    if (!h->small.p) return SPGEMM_OK;
+    if (!h->status.p) return SPGEMM_OK;
     TSG_CHECK(cudaStreamSynchronize(h->last_stream));
-    const size_t o_status = align16(4 * (kMaxBins + 2)) + align16(4 * (kMaxBins + 3)) + align16(4 * (kMaxBins + 2));
     unsigned st = 0;
-    TSG_CHECK(cudaMemcpy(&st, static_cast<char*>(h->small.p) + o_status, 4, cudaMemcpyDeviceToHost));
-    TSG_CHECK(cudaMemset(static_cast<char*>(h->small.p) + o_status, 0, 4));
+    TSG_CHECK(cudaMemcpy(&st, h->status.p, 4, cudaMemcpyDeviceToHost));
+    TSG_CHECK(cudaMemset(h->status.p, 0, 4));
     if (st & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
     if (st & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;
     if (st & kStatusInternal) return SPGEMM_ERR_INTERNAL;
