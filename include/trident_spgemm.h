@@ -237,6 +237,34 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
 spgemm_status spgemm_trident_schedule(int32_t q, int32_t lambda, int32_t* a_tile, int32_t* b_tile,
                                       int32_t* group_ptr);
 
+/* ------------------------------------------------------------ differentiation
+ *
+ * spgemm_backward: gradients of a scalar loss L through C = A B with the
+ * sparsity patterns held fixed (chain rule on C_ij = sum_k a_ik b_kj, Sec. 2):
+ *   dA_ik = sum_{j in B_k} G_ij b_kj       for (i,k) in pattern(A)
+ *   dB_kj = sum_{i: k in A_i} a_ik G_ij    for (k,j) in pattern(B)
+ * where G_ij = dL/dC_ij is given as C->val on the pattern of C (C->row_ptr
+ * and C->col_idx as returned by the forward product of the same A, B).
+ * dA (device, nnz(A) values) and dB (device, nnz(B) values) may each be
+ * NULL to skip.  dA is summed over B row k in stored order (deterministic).
+ * deterministic == 0: dB by atomic scatter (fast; summation order not
+ * fixed).  deterministic != 0: dB from the transpose of A (built in the
+ * handle's workspace), each entry summed over i ascending.  Asynchronous.
+ * A column of B's row k that is missing from row i of C latches
+ * SPGEMM_ERR_INTERNAL (C is not the product's pattern).
+ */
+spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
+                              const spgemm_csr_in* B, const spgemm_csr_in* C, void* dA, void* dB,
+                              int32_t deterministic, spgemm_stream_t stream);
+
+/* spgemm_csr_transpose: XT = X^T.  XT->nrows = X->ncols, XT->ncols =
+ * X->nrows; XT->row_ptr (X->ncols + 1), XT->col_idx and XT->val (X->nnz
+ * each; val skipped when X->val is NULL) are caller-allocated.  Rows of XT
+ * come out sorted (X must have no repeated column within a row).
+ * Asynchronous; workspace from the handle. */
+spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
+                                   spgemm_csr_out* XT, spgemm_stream_t stream);
+
 /* --------------------------------------------------------- instrumentation */
 
 /* Number of kernels this handle has launched since creation (host counter). */

@@ -69,6 +69,9 @@ SIGNATURES = {
                            ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),
     "spgemm_trident_schedule": ([I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
                                 ctypes.c_int),
+    "spgemm_backward": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, P,
+                         I32, P], ctypes.c_int),
+    "spgemm_csr_transpose": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

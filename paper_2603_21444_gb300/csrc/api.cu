@@ -52,6 +52,7 @@ struct spgemm_handle {
     DevBuf small;
     DevBuf dense;
     DevBuf status;  // the device status word latched by kernels
+    DevBuf tr;      // transpose work and the A^T of the deterministic backward
     void* pinned = nullptr;
     size_t pinned_n = 0;
     // plan cache (bin lists of the last sizing call)
@@ -545,6 +546,7 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->small.p) cudaFree(h->small.p);
     if (h->dense.p) cudaFree(h->dense.p);
     if (h->status.p) cudaFree(h->status.p);
+    if (h->tr.p) cudaFree(h->tr.p);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -775,6 +777,107 @@ spgemm_status spgemm_trident_schedule(int32_t q, int32_t lambda, int32_t* a_tile
                 }
             }
     group_ptr[g] = t;
+    return SPGEMM_OK;
+}
+
+namespace {
+
+// X^T into the given arrays, work from h->tr starting at byte offset `off`
+spgemm_status transpose_into(spgemm_handle* h, int dtype, const spgemm_csr_in* X, int* trp, int* tcol, void* tval,
+                             size_t off, cudaStream_t st) {
+    const long long nnz = X->nnz, nc = X->ncols;
+    const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
+    const long long nblk = scan_blocks(std::max<long long>(nc, 1));
+    const size_t o_work = off;
+    const size_t o_ex = o_work + align16(4 * std::max<long long>(nc, 1));
+    const size_t o_bsum = o_ex + align16(8 * (nc + 1));
+    const size_t o_tmp = o_bsum + align16(8 * nblk);
+    const size_t bytes = o_tmp + align16(4 * std::max<long long>(nnz, 1)) + align16(esz * std::max<long long>(nnz, 1));
+    TSG_TRY(grow(h->tr, bytes));
+    char* b = static_cast<char*>(h->tr.p);
+    PhaseScope ps(h, 6, st);
+    TSG_CHECK(launch_transpose(dtype, X->row_ptr, X->col_idx, X->val, X->nrows, X->ncols, nnz, trp, tcol, tval,
+                               reinterpret_cast<int*>(b + o_work), b + o_tmp, reinterpret_cast<long long*>(b + o_bsum),
+                               reinterpret_cast<long long*>(b + o_ex), h->sms, st));
+    h->launches += 7;
+    return SPGEMM_OK;
+}
+
+}  // namespace
+
+spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
+                                   spgemm_csr_out* XT, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(X, false) || !XT || !XT->row_ptr || (X->nnz > 0 && !XT->col_idx))
+        return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (XT->nrows != X->ncols || XT->ncols != X->nrows) return SPGEMM_ERR_SHAPE;
+    if (X->val && X->nnz > 0 && !XT->val) return SPGEMM_ERR_INVALID_ARG;
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    return transpose_into(h, dtype, X, XT->row_ptr, XT->col_idx, X->val ? XT->val : nullptr, 0, st);
+}
+
+spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
+                              const spgemm_csr_in* B, const spgemm_csr_in* C, void* dA, void* dB,
+                              int32_t deterministic, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(A, true) || !csr_in_ok(B, true) || !csr_in_ok(C, true)) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    TSG_TRY(grow(h->status, 16, st, true));
+    BwdArgs a{};
+    a.m = A->nrows;
+    a.kdim = B->nrows;
+    a.nnzb = B->nnz;
+    a.arp = A->row_ptr;
+    a.acol = A->col_idx;
+    a.aval = A->val;
+    a.brp = B->row_ptr;
+    a.bcol = B->col_idx;
+    a.bval = B->val;
+    a.crp = C->row_ptr;
+    a.ccol = C->col_idx;
+    a.g = C->val;
+    a.da = dA;
+    a.db = dB;
+    a.scatter_db = deterministic ? 0 : 1;
+    a.status = static_cast<unsigned*>(h->status.p);
+    if (dB && deterministic) {
+        // A^T (kdim rows) at the front of h->tr, transpose work after it
+        const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
+        const long long nnz = std::max(A->nnz, 1);
+        const size_t o_rp = 0;
+        const size_t o_col = o_rp + align16(4 * ((long long)A->ncols + 1));
+        const size_t o_val = o_col + align16(4 * nnz);
+        const size_t o_work = o_val + align16(esz * nnz);
+        TSG_TRY(grow(h->tr, o_work + 16));
+        // the transpose may grow h->tr: compute pointers after it returns
+        int* trp = nullptr;
+        {
+            // grow first to the full size the transpose needs, then place A^T
+            const long long nblk = scan_blocks(std::max(A->ncols, 1));
+            const size_t need = o_work + align16(4 * std::max(A->ncols, 1)) + align16(8 * ((long long)A->ncols + 1)) +
+                                align16(8 * nblk) + align16(4 * nnz) + align16(esz * nnz);
+            TSG_TRY(grow(h->tr, need));
+            char* b = static_cast<char*>(h->tr.p);
+            trp = reinterpret_cast<int*>(b + o_rp);
+            a.trp = trp;
+            a.tcol = reinterpret_cast<int*>(b + o_col);
+            a.tval = b + o_val;
+        }
+        TSG_TRY(transpose_into(h, dtype, A, const_cast<int*>(a.trp), const_cast<int*>(a.tcol),
+                               const_cast<void*>(a.tval), o_work, st));
+    }
+    PhaseScope ps(h, 6, st);
+    TSG_CHECK(launch_backward(dtype, a, h->sms, st));
+    h->launches += 2;
     return SPGEMM_OK;
 }
 

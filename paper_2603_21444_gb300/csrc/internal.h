@@ -64,6 +64,36 @@ cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& a, void* dense, int
                              cudaStream_t s);
 int heavy_chunk_for(int ncols);
 
+// int64 exclusive sums -> int32 (rows_misc.cu)
+cudaError_t launch_ll_to_int(const long long* src, long long n, int* dst, cudaStream_t s);
+
+// backward (backward.cu)
+struct BwdArgs {
+    int m;                 // rows of A (= rows of C)
+    int kdim;              // rows of B (= columns of A)
+    long long nnzb;        // nnz(B)
+    const int* arp;
+    const int* acol;
+    const void* aval;
+    const int* brp;
+    const int* bcol;
+    const void* bval;
+    const int* crp;        // pattern of C
+    const int* ccol;
+    const void* g;         // upstream gradient on pat(C)
+    void* da;              // nnz(A) or null
+    void* db;              // nnz(B) or null
+    int scatter_db;        // 1: atomic scatter; 0: from A^T (deterministic)
+    const int* trp;        // A^T (kdim rows), rows sorted
+    const int* tcol;
+    const void* tval;
+    unsigned* status;
+};
+cudaError_t launch_backward(int dtype, const BwdArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_transpose(int dtype, const int* rp, const int* col, const void* val, int nrows, int ncols,
+                             long long nnz, int* trp, int* tcol, void* tval, int* work, void* workv, long long* bsum,
+                             long long* ex, int sms, cudaStream_t s);
+
 // trident partition (partition.cu)
 cudaError_t launch_split_count(const int* rp, const int* col, int nrows, const int* cb, int ncp, int* counts,
                                cudaStream_t s);

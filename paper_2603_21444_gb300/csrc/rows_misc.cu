@@ -216,6 +216,17 @@ cudaError_t launch_rowptr(const GroupDev* groups, const long long* unit_base, in
     return cudaGetLastError();
 }
 
+__global__ void k_ll_to_int(const long long* __restrict__ src, long long n, int* dst) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (int)src[i];
+}
+
+cudaError_t launch_ll_to_int(const long long* src, long long n, int* dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_ll_to_int<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- validation
 
 __global__ void k_validate(const int* __restrict__ rp, const int* __restrict__ col, int nrows, int ncols, int nnz,
