@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--d", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--extras", dest="extras", action="store_true", default=True,
+                   help="also time the trident grid, 256 products and the autograd workload")
+    p.add_argument("--no-extras", dest="extras", action="store_false")
     return p.parse_args()
 
 
@@ -278,6 +281,15 @@ def run_native(args):
                 "roofline": roof, "phases": {k: (round(v, 4) if isinstance(v, float) else v)
                                               for k, v in phases.items()},
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        if args.extras and world == 1:
+            extras = {}
+            for name, fn in (("trident_grid", bench_trident), ("many_products", bench_many),
+                             ("autograd", bench_autograd)):
+                try:
+                    extras[name] = fn(tsg, max(3, args.steps // 4))
+                except Exception as ex:  # report, keep the main line
+                    extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            line["workloads"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -322,6 +334,139 @@ def e2e_public_api(tsg, A, B, prods, args):
     h.close()
     return {"value": round(2 * prods / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3), "steps": steps}
+
+
+def _time(fn, steps, warmup=1, stream=None):
+    """Mean ms of fn() over `steps` calls (CUDA events, after warm-up)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_trident(tsg, steps):
+    """ER A, B with n = 2^21 and 32 per row, float64, on the trident grid
+    4 x 4 x lambda=4: 256 block products, 64 output blocks of 4 rounds."""
+    import torch
+    import gen
+    n, d, q, lam = 1 << 21, 32, 4, 4
+    A = gen.er(n, n, d, 4)
+    B = gen.er(n, n, d, 5)
+    prods = products(A, B)
+    dA, dB = tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B)
+    del A, B
+    h = tsg.Handle()
+    t_split = _time(lambda: tsg.TridentPlan(dA, dB, q, lam, h), 1, warmup=1)
+    plan = tsg.TridentPlan(dA, dB, q, lam, h)
+    out = {"workload": "ER A*B n=2^21 d=32 f64, trident 4x4x4 (256 block products, 64 blocks)",
+           "products": prods, "partition_ms": round(t_split, 3)}
+    # fused, persistent: sized once, numeric replayed from a CUDA graph
+    fp = plan.fused_plan()
+    fp.execute(True)
+    torch.cuda.synchronize()
+    t_replay = _time(lambda: fp.execute(True), steps)
+    out["batched_graph_ms"] = round(t_replay, 3)
+    out["batched_graph_gflops"] = round(2 * prods / t_replay / 1e6, 2)
+    out["nnz_c"] = int(sum(fp.nnz))
+    # fused, fresh: sizing + numeric every step
+    fresh = lambda: tsg.Plan(plan.As, plan.Bs, plan.group_ptr).execute(False)
+    t_fresh = _time(fresh, max(1, steps // 4))
+    out["batched_fresh_ms"] = round(t_fresh, 3)
+    out["batched_fresh_gflops"] = round(2 * prods / t_fresh / 1e6, 2)
+    del fp
+    plan.fused = None
+    torch.cuda.empty_cache()
+    # unfused: partials materialised, then one ordered merge per block
+    t_unf = _time(lambda: plan.run_unfused(), 1)
+    out["unfused_ms"] = round(t_unf, 3)
+    plan.partials = None
+    torch.cuda.empty_cache()
+    # plain: the per-block loop, one product call per round, one merge per block
+    t_plain = _time(lambda: plan.run_plain(), 1, warmup=0)
+    out["plain_per_block_ms"] = round(t_plain, 3)
+    out["plain_per_block_gflops"] = round(2 * prods / t_plain / 1e6, 2)
+    out["speedup_batched_fresh_vs_plain"] = round(t_plain / t_fresh, 2)
+    out["speedup_batched_graph_vs_plain"] = round(t_plain / t_replay, 2)
+    h.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_many(tsg, steps):
+    """256 independent ER products, n log-uniform in [2^10, 2^16], 4..64 per
+    row, float64: one plan (one graph launch) against 256 product calls."""
+    import torch
+    import gen
+    pairs = gen.er_batch(256)
+    prods = sum(products(a, b) for a, b in pairs)
+    As = [tsg.DeviceCSR.from_host(a) for a, _ in pairs]
+    Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
+    h = tsg.Handle()
+    plan = tsg.Plan(As, Bs)
+    default_ms = _time(lambda: plan.execute(True), steps)
+    tuned = plan.autotune()
+    plan.execute(True)
+    tuned_ms = _time(lambda: plan.execute(True), steps)
+    fresh_ms = _time(lambda: tsg.Plan(As, Bs).execute(False), max(1, steps // 4))
+    loop_ms = _time(lambda: [tsg.spgemm(a, b, h) for a, b in zip(As, Bs)], 1)
+    out = {"workload": "256 ER products, n=2^U(10,16), d=U{4..64}, f64", "products": prods,
+           "batched_graph_ms": round(default_ms, 3), "batched_graph_autotuned_ms": round(tuned_ms, 3),
+           "autotune": {"num_bins": tuned.num_bins, "bin_upper": list(tuned.bin_upper)[:tuned.num_bins],
+                        "bin_kernel": list(tuned.bin_kernel)[:tuned.num_bins],
+                        "warps_per_block": tuned.warps_per_block},
+           "batched_fresh_ms": round(fresh_ms, 3), "plain_256_calls_ms": round(loop_ms, 3),
+           "batched_graph_gflops": round(2 * prods / min(default_ms, tuned_ms) / 1e6, 2),
+           "speedup_batched_fresh_vs_plain": round(loop_ms / fresh_ms, 2)}
+    plan.close()
+    h.close()
+    return out
+
+
+def bench_autograd(tsg, steps):
+    """A 2^18 x 2^18, B 2^18 x 2^16, 16 per row, float32 N(0,1); loss =
+    sum(C * W): forward and hand-written backward on fixed patterns."""
+    import torch
+    import gen
+    from paper_2603_21444_gb300 import autograd as ag
+    A = gen.er(1 << 18, 1 << 18, 16, 5, np.float32, "normal")
+    B = gen.er(1 << 18, 1 << 16, 16, 6, np.float32, "normal")
+    prods = products(A, B)
+    dA, dB = tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B)
+    h = tsg.Handle()
+    pat = ag.Pattern(dA, dB, h)
+    a = dA.val.clone().requires_grad_(True)
+    b = dB.val.clone().requires_grad_(True)
+    W = torch.randn(pat.C.nnz, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+
+    def fwd():
+        return ag.spgemm_values(a, b, pat)
+
+    def fwd_bwd():
+        a.grad = None
+        b.grad = None
+        (fwd() * W).sum().backward()
+
+    fwd_ms = _time(fwd, steps)
+    fb_ms = _time(fwd_bwd, steps)
+    c = fwd()
+    g = W
+    bwd_ms = _time(lambda: ag.backward(dA, dB, pat.C, g, handle=h), steps)
+    det_ms = _time(lambda: ag.backward(dA, dB, pat.C, g, deterministic=True, handle=h), max(1, steps // 2))
+    fresh_ms = _time(lambda: tsg.spgemm(dA, dB, h), steps)
+    h.close()
+    del c
+    return {"workload": "A 2^18x2^18, B 2^18x2^16, d=16, f32, loss sum(C*W)", "products": prods,
+            "nnz_c": pat.C.nnz, "forward_ms": round(fwd_ms, 3), "forward_with_sizing_ms": round(fresh_ms, 3),
+            "backward_ms": round(bwd_ms, 3), "backward_deterministic_ms": round(det_ms, 3),
+            "fwd_plus_bwd_ms": round(fb_ms, 3), "forward_gflops": round(2 * prods / fwd_ms / 1e6, 2)}
 
 
 def main():

@@ -200,6 +200,39 @@ spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst
                              const int32_t* group_ptr, spgemm_csr_out* C, int64_t* c_nnz,
                              const spgemm_tune* tune, spgemm_stream_t stream);
 
+/* ------------------------------------------------ persistent batched plan
+ *
+ * A plan is one batched problem (the arguments of spgemm_batched) sized once
+ * and executed many times.  It owns a private workspace (bin lists,
+ * descriptors, accumulators), so executing it is independent of other calls.
+ *
+ * spgemm_plan_create: runs the sizing pass: writes c_row_ptr[g] (host array
+ * of ngroups device pointers, each nrows+1 int32) and c_nnz[g] (host),
+ * synchronising once.  The inputs must stay allocated and unchanged for the
+ * plan's lifetime.  tune NULL = library defaults.
+ * spgemm_plan_execute: the numeric pass into C[g] (row_ptr as sized,
+ * col_idx / val of c_nnz[g] entries).  use_graph != 0: the first execution
+ * for a given set of output pointers runs the kernels directly and also
+ * captures them into a CUDA graph owned by the plan; later executions with
+ * the same outputs are one cudaGraphLaunch.  Asynchronous.
+ * spgemm_plan_autotune: times candidate bin layouts and warps-per-block
+ * settings on this problem (each candidate sized and executed into C, which
+ * must be allocated), keeps the fastest in the plan and writes it to *chosen
+ * (may be NULL).  Results are cached per device, dtype and product-count
+ * histogram.  Every candidate gives the same output bits.  Synchronises.
+ */
+typedef struct spgemm_plan spgemm_plan;
+spgemm_status spgemm_plan_create(spgemm_dtype dtype, int32_t ninst, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                 int32_t ngroups, const int32_t* group_ptr, int32_t* const* c_row_ptr,
+                                 int64_t* c_nnz, const spgemm_tune* tune, spgemm_stream_t stream,
+                                 spgemm_plan** out);
+spgemm_status spgemm_plan_execute(spgemm_plan* p, const spgemm_csr_out* C, int32_t use_graph,
+                                  spgemm_stream_t stream);
+spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spgemm_stream_t stream,
+                                   spgemm_tune* chosen);
+spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count);
+spgemm_status spgemm_plan_destroy(spgemm_plan* p);
+
 /* ------------------------------------------ trident partition (Sec. 3.2)
  *
  * spgemm_tile_split: cut X into nrp x ncp tiles.  Tile (rp, cp) holds rows

@@ -5,5 +5,5 @@ sum of trident partial products, the batched trident grid on one GPU and the
 autograd backward, all computed by hand-written CUDA kernels behind the C ABI
 in include/trident_spgemm.h.  PyTorch supplies device memory and streams.
 """
-from .api import (BatchPlan, DeviceCSR, Handle, TridentPlan, batched, default_handle, default_tune,  # noqa: F401
+from .api import (BatchPlan, DeviceCSR, Handle, Plan, TridentPlan, batched, default_handle, default_tune,  # noqa: F401
                   merge, numeric_into, spgemm, symbolic, tile_split, trident_bounds, trident_schedule)

@@ -72,6 +72,12 @@ SIGNATURES = {
     "spgemm_backward": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, P,
                          I32, P], ctypes.c_int),
     "spgemm_csr_transpose": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
+    "spgemm_plan_create": ([ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), I32, ctypes.POINTER(I32),
+                            ctypes.POINTER(P), I64P, ctypes.POINTER(Tune), P, ctypes.POINTER(P)], ctypes.c_int),
+    "spgemm_plan_execute": ([P, ctypes.POINTER(CsrOut), I32, P], ctypes.c_int),
+    "spgemm_plan_autotune": ([P, ctypes.POINTER(CsrOut), P, ctypes.POINTER(Tune)], ctypes.c_int),
+    "spgemm_plan_launch_count": ([P, I64P], ctypes.c_int),
+    "spgemm_plan_destroy": ([P], ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

@@ -323,6 +323,69 @@ def trident_schedule(q: int, lam: int):
     return list(a), list(b), list(gp)
 
 
+class Plan:
+    """A batched problem sized once (``spgemm_plan_create``) and executed many
+    times (``spgemm_plan_execute``, replayed from a CUDA graph)."""
+
+    def __init__(self, As: list[DeviceCSR], Bs: list[DeviceCSR], group_ptr: list[int] | None = None,
+                 tune: Tune | None = None, stream=None):
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need equally many A and B instances")
+        self.As, self.Bs = As, Bs
+        self.ninst = len(As)
+        self.group_ptr = list(group_ptr) if group_ptr is not None else list(range(self.ninst + 1))
+        self.ngroups = len(self.group_ptr) - 1
+        self.dtype = As[0].val.dtype
+        self.a_arr = (CsrIn * self.ninst)(*[a.as_in() for a in As])
+        self.b_arr = (CsrIn * self.ninst)(*[b.as_in() for b in Bs])
+        self.gp = (ctypes.c_int32 * (self.ngroups + 1))(*self.group_ptr)
+        dev = As[0].row_ptr.device
+        rps = [torch.empty(As[self.group_ptr[g]].nrows + 1, dtype=torch.int32, device=dev)
+               for g in range(self.ngroups)]
+        rp_arr = (ctypes.c_void_p * self.ngroups)(*[r.data_ptr() for r in rps])
+        nnz = (ctypes.c_int64 * self.ngroups)()
+        self._p = ctypes.c_void_p()
+        check(_abi.lib().spgemm_plan_create(_dtype_code(self.dtype), self.ninst, self.a_arr, self.b_arr,
+                                            self.ngroups, self.gp, rp_arr, nnz,
+                                            ctypes.byref(tune) if tune is not None else None, _stream(stream),
+                                            ctypes.byref(self._p)), "spgemm_plan_create")
+        self.nnz = [int(x) for x in nnz]
+        self.C = []
+        for g in range(self.ngroups):
+            t = self.group_ptr[g]
+            self.C.append(DeviceCSR(As[t].nrows, Bs[t].ncols, rps[g],
+                                    torch.empty(self.nnz[g], dtype=torch.int32, device=dev),
+                                    torch.empty(self.nnz[g], dtype=self.dtype, device=dev)))
+        self.outs = (CsrOut * self.ngroups)(*[C.as_out() for C in self.C])
+
+    def execute(self, use_graph: bool = True, stream=None):
+        check(_abi.lib().spgemm_plan_execute(self._p, self.outs, 1 if use_graph else 0, _stream(stream)),
+              "spgemm_plan_execute")
+        return self.C
+
+    def autotune(self, stream=None) -> Tune:
+        t = Tune()
+        check(_abi.lib().spgemm_plan_autotune(self._p, self.outs, _stream(stream), ctypes.byref(t)),
+              "spgemm_plan_autotune")
+        return t
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int64()
+        check(_abi.lib().spgemm_plan_launch_count(self._p, ctypes.byref(c)), "spgemm_plan_launch_count")
+        return int(c.value)
+
+    def close(self):
+        if self._p:
+            _abi.lib().spgemm_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class TridentPlan:
     """The trident grid q x q x lambda of C = A B on one device.
 
@@ -331,10 +394,12 @@ class TridentPlan:
     partial A_{i r' k} B_{r' j} uses the whole tile B_{r' j} (the allgather of
     Alg. 2 is the tile itself on one device).
 
-    mode "fused": one batched call, each output row accumulates its q rounds
-    at once (partials never materialised).  mode "unfused": every partial is
-    a separate instance written to memory, then each block is the ordered sum
-    of its partials (the paper's spgeam step).  Both give identical bits.
+    fused: one batched problem whose output rows accumulate their q rounds at
+    once (partials never materialised), sized once, executed from a CUDA
+    graph.  unfused: every partial is its own output, then each block is the
+    ordered sum of its partials (the paper's spgeam step).  plain: the
+    per-block loop of the paper's local step, one product call per round and
+    one merge per block.  All three give identical bits.
     """
 
     def __init__(self, A: DeviceCSR, B: DeviceCSR, q: int, lam: int, handle: Handle | None = None):
@@ -350,18 +415,31 @@ class TridentPlan:
         self.As = [self.A_tiles[t // q][t % q] for t in a_t]
         self.Bs = [self.B_tiles[t // q][t % q] for t in b_t]
         self.group_ptr = gp
-        self.fused = BatchPlan(self.As, self.Bs, gp)
+        self.fused = None
         self.partials = None
 
     def block_index(self, i: int, j: int, k: int) -> int:
         return (i * self.q + j) * self.lam + k
 
-    def run_fused(self, tune: Tune | None = None, stream=None):
-        return self.fused.run(self.h, tune, stream)
+    def fused_plan(self, tune: Tune | None = None) -> Plan:
+        if self.fused is None:
+            self.fused = Plan(self.As, self.Bs, self.group_ptr, tune)
+        return self.fused
 
-    def run_unfused(self, tune: Tune | None = None, stream=None):
+    def run_fused(self, use_graph: bool = True, stream=None):
+        return self.fused_plan().execute(use_graph, stream)
+
+    def run_unfused(self, stream=None):
         if self.partials is None:
-            self.partials = BatchPlan(self.As, self.Bs)
-        P = self.partials.run(self.h, tune, stream)
+            self.partials = Plan(self.As, self.Bs)
+        P = self.partials.execute(True, stream)
         return [merge(P[self.group_ptr[g]:self.group_ptr[g + 1]], self.h, stream)
                 for g in range(len(self.group_ptr) - 1)]
+
+    def run_plain(self, stream=None):
+        out = []
+        for g in range(len(self.group_ptr) - 1):
+            parts = [spgemm(self.As[t], self.Bs[t], self.h, stream)
+                     for t in range(self.group_ptr[g], self.group_ptr[g + 1])]
+            out.append(merge(parts, self.h, stream))
+        return out

@@ -68,6 +68,10 @@ struct spgemm_handle {
     int occ_sym[kNumVariants];
     int occ_num[2][kNumVariants];
     std::vector<cudaStream_t> streams_used;
+    // the last descriptor block copied to the device (identical blocks are
+    // not copied again, so a repeated fill call launches kernels only)
+    std::vector<char> last_stage;
+    const void* last_stage_dst = nullptr;
 };
 
 namespace {
@@ -288,7 +292,10 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     size_t o_inst = o_ubase + align16(8 * (ngroups + 1));
     size_t o_groups = o_inst + align16(sizeof(InstDev) * ninst);
     size_t small_bytes = o_groups + align16(sizeof(GroupDev) * ngroups);
-    if (h->small.n < small_bytes) h->plan_valid = false;
+    if (h->small.n < small_bytes) {
+        h->plan_valid = false;
+        h->last_stage_dst = nullptr;
+    }
     TSG_TRY(grow(h->small, small_bytes));
     char* sb = static_cast<char*>(h->small.p);
     int* d_hist = reinterpret_cast<int*>(sb + o_hist);
@@ -315,7 +322,11 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         std::memcpy(stage.data(), unit_base.data(), 8 * (ngroups + 1));
         if (ninst) std::memcpy(stage.data() + (o_inst - o_ubase), inst.data(), sizeof(InstDev) * ninst);
         std::memcpy(stage.data() + (o_groups - o_ubase), groups.data(), sizeof(GroupDev) * ngroups);
-        TSG_CHECK(cudaMemcpyAsync(sb + o_ubase, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
+        if (h->last_stage_dst != sb + o_ubase || h->last_stage != stage) {
+            TSG_CHECK(cudaMemcpyAsync(sb + o_ubase, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
+            h->last_stage.swap(stage);
+            h->last_stage_dst = sb + o_ubase;
+        }
     }
     // ---- plan signature (input patterns, output row_ptr, bins)
     uint64_t sig = 1469598103934665603ull;
@@ -725,6 +736,7 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
     size_t o_cb = o_rb + align16(4 * (nrp + 1));
     size_t bytes = o_cb + align16(4 * (ncp + 1));
     TSG_TRY(grow(h->small, bytes));
+    h->last_stage_dst = nullptr;
     char* sb = static_cast<char*>(h->small.p);
     std::vector<char> stage(bytes - o_ubase);
     std::memcpy(stage.data(), ubase.data(), 8 * (nt + 1));
@@ -929,6 +941,269 @@ spgemm_status spgemm_read_timing(spgemm_handle* h, double* ms, int64_t* count) {
     }
     h->pending.clear();
     return rc;
+}
+
+}  // extern "C"
+
+// ===================================================================== plans
+
+#include <map>
+#include <mutex>
+
+struct spgemm_plan {
+    spgemm_handle* h = nullptr;  // private workspace
+    int dtype = 1;
+    std::vector<InstDev> inst;
+    std::vector<GroupDev> groups;
+    spgemm_tune tune{};
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> exec_key;
+    int64_t graph_kernels = 0;  // kernels in the captured graph
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<uint64_t, spgemm_tune> g_tune_cache;
+
+spgemm_status plan_bind(spgemm_plan* p, const spgemm_csr_out* C, std::vector<const void*>* key) {
+    key->clear();
+    for (size_t g = 0; g < p->groups.size(); ++g) {
+        const spgemm_csr_out& Cg = C[g];
+        if (Cg.row_ptr != p->groups[g].crp || Cg.nrows != p->groups[g].nrows || Cg.ncols != p->groups[g].ncols)
+            return SPGEMM_ERR_SHAPE;
+        p->groups[g].ccol = Cg.col_idx;
+        p->groups[g].cval = Cg.val;
+        key->push_back(Cg.col_idx);
+        key->push_back(Cg.val);
+    }
+    return SPGEMM_OK;
+}
+
+spgemm_status plan_size(spgemm_plan* p, int64_t* c_nnz, cudaStream_t st) {
+    std::vector<GroupDev> g = p->groups;
+    for (GroupDev& G : g) {
+        G.ccol = nullptr;
+        G.cval = nullptr;
+    }
+    std::vector<int64_t> tmp(g.size());
+    return run(p->h, p->dtype, false, p->inst, g, true, c_nnz ? c_nnz : tmp.data(), p->tune, {}, st);
+}
+
+void plan_drop_graph(spgemm_plan* p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+    p->exec_key.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+spgemm_status spgemm_plan_create(spgemm_dtype dtype, int32_t ninst, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                 int32_t ngroups, const int32_t* group_ptr, int32_t* const* c_row_ptr,
+                                 int64_t* c_nnz, const spgemm_tune* tune, spgemm_stream_t stream,
+                                 spgemm_plan** out) {
+    if (!out || ninst < 1 || ninst > (1 << 20) || !A || !B || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (group_ptr == nullptr) {
+        if (ngroups != ninst) return SPGEMM_ERR_INVALID_ARG;
+    } else if (ngroups < 1 || group_ptr[0] != 0 || group_ptr[ngroups] != ninst) {
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    spgemm_tune tn;
+    default_tune(&tn);
+    if (tune) {
+        TSG_TRY(check_tune(tune));
+        tn = *tune;
+    }
+    tn.validate = 0;
+    spgemm_plan* p = new (std::nothrow) spgemm_plan();
+    if (!p) return SPGEMM_ERR_OOM;
+    p->dtype = dtype;
+    p->tune = tn;
+    for (int g = 0; g < ngroups; ++g) {
+        const int t0 = group_ptr ? group_ptr[g] : g;
+        const int t1 = group_ptr ? group_ptr[g + 1] : g + 1;
+        if (t1 <= t0 || t1 - t0 > kMaxGroupInst || !c_row_ptr[g]) {
+            delete p;
+            return SPGEMM_ERR_INVALID_ARG;
+        }
+        for (int t = t0; t < t1; ++t) {
+            if (!csr_in_ok(A + t, true) || !csr_in_ok(B + t, true)) {
+                delete p;
+                return SPGEMM_ERR_INVALID_ARG;
+            }
+            if (A[t].ncols != B[t].nrows || A[t].nrows != A[t0].nrows || B[t].ncols != B[t0].ncols) {
+                delete p;
+                return SPGEMM_ERR_SHAPE;
+            }
+        }
+        p->groups.push_back({t0, t1 - t0, A[t0].nrows, B[t0].ncols, c_row_ptr[g], nullptr, nullptr, 0});
+    }
+    for (int t = 0; t < ninst; ++t)
+        p->inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val});
+    spgemm_status rc = spgemm_create(&p->h);
+    if (rc == SPGEMM_OK) rc = plan_size(p, c_nnz, reinterpret_cast<cudaStream_t>(stream));
+    if (rc != SPGEMM_OK) {
+        spgemm_destroy(p->h);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_execute(spgemm_plan* p, const spgemm_csr_out* C, int32_t use_graph,
+                                  spgemm_stream_t stream) {
+    if (!p || !C) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<const void*> key;
+    TSG_TRY(plan_bind(p, C, &key));
+    if (use_graph && p->exec && key == p->exec_key) {
+        TSG_CHECK(cudaGraphLaunch(p->exec, st));
+        p->h->launches += p->graph_kernels;
+        return SPGEMM_OK;
+    }
+    TSG_TRY(run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st));
+    if (!use_graph || !p->h->plan_valid) return SPGEMM_OK;
+    // capture the same fill: descriptors and bin lists are already in place,
+    // so the captured work is kernel launches only
+    plan_drop_graph(p);
+    const bool timing = p->h->timing;
+    p->h->timing = false;
+    TSG_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = p->h->launches;
+    spgemm_status rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);
+    p->graph_kernels = p->h->launches - before;
+    p->h->launches = before;  // captured, not launched
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    p->h->timing = timing;
+    if (rc != SPGEMM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    TSG_CHECK(e);
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        p->exec = nullptr;
+        return cuda_status(e);
+    }
+    p->exec_key = key;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spgemm_stream_t stream,
+                                   spgemm_tune* chosen) {
+    if (!p || !C) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<const void*> key;
+    TSG_TRY(plan_bind(p, C, &key));
+    plan_drop_graph(p);
+    // cache key: device, dtype, the problem's product-count histogram
+    TSG_TRY(plan_size(p, nullptr, st));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint64_t sig = 1469598103934665603ull;
+    sig = fnv(sig, &dev, sizeof(dev));
+    sig = fnv(sig, &p->dtype, sizeof(p->dtype));
+    for (int v : p->h->plan_hist) {
+        // histogram shape on a log scale: tunes transfer between similar problems
+        int lg = 0;
+        while ((1 << lg) < v) ++lg;
+        sig = fnv(sig, &lg, sizeof(lg));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) {
+            p->tune = it->second;
+            if (chosen) *chosen = p->tune;
+            return plan_size(p, nullptr, st);
+        }
+    }
+    std::vector<spgemm_tune> cand;
+    spgemm_tune base;
+    default_tune(&base);
+    for (int wpb : {8, 4, 16}) {
+        spgemm_tune t = base;
+        t.warps_per_block = wpb;
+        cand.push_back(t);
+    }
+    {
+        // one size up: every bin served by the next larger variant
+        spgemm_tune t = base;
+        for (int b = 0; b + 1 < t.num_bins; ++b) t.bin_kernel[b] = b + 1;
+        cand.push_back(t);
+    }
+    {
+        // coarse: four bins
+        spgemm_tune t = base;
+        const int up[4] = {128, 512, 2048, 8192};
+        const int kv[4] = {2, 4, 6, 8};
+        t.num_bins = 4;
+        for (int b = 0; b < 4; ++b) {
+            t.bin_upper[b] = up[b];
+            t.bin_kernel[b] = kv[b];
+        }
+        cand.push_back(t);
+    }
+    cudaEvent_t e0, e1;
+    TSG_CHECK(cudaEventCreate(&e0));
+    TSG_CHECK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    spgemm_tune best_t = base;
+    spgemm_status rc = SPGEMM_OK;
+    for (const spgemm_tune& t : cand) {
+        p->tune = t;
+        p->tune.validate = 0;
+        rc = plan_size(p, nullptr, st);
+        if (rc != SPGEMM_OK) break;
+        rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);  // warm
+        if (rc != SPGEMM_OK) break;
+        float tbest = 1e30f;
+        for (int rep = 0; rep < 3 && rc == SPGEMM_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tbest = std::min(tbest, ms);
+        }
+        if (rc != SPGEMM_OK) break;
+        if (tbest < best) {
+            best = tbest;
+            best_t = p->tune;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SPGEMM_OK) return rc;
+    p->tune = best_t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[sig] = best_t;
+    }
+    if (chosen) *chosen = best_t;
+    return plan_size(p, nullptr, st);
+}
+
+spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count) {
+    if (!p || !count) return SPGEMM_ERR_INVALID_ARG;
+    *count = p->h->launches;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_destroy(spgemm_plan* p) {
+    if (!p) return SPGEMM_OK;
+    plan_drop_graph(p);
+    spgemm_destroy(p->h);
+    delete p;
+    return SPGEMM_OK;
 }
 
 }  // extern "C"

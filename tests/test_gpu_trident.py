@@ -129,8 +129,15 @@ def test_trident_plan_fused_and_unfused(tsg, handle, q, lam):
     B = gen.er(n, n, d, 5, np.float64, "uniform")
     ref, _ = oracle.trident_product(A, B, q, lam)
     plan = tsg.TridentPlan(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), q, lam, handle)
-    fused = plan.run_fused()
+    fused = plan.run_fused(use_graph=False)
+    for C in fused:
+        C.val.zero_()
+    fused = plan.run_fused(use_graph=True)       # direct run + capture
+    for C in fused:
+        C.val.zero_()
+    fused = plan.run_fused(use_graph=True)       # graph replay
     unfused = plan.run_unfused()
+    plain = plan.run_plain()
     torch.cuda.synchronize()
     for i in range(q):
         for j in range(q):
@@ -138,3 +145,28 @@ def test_trident_plan_fused_and_unfused(tsg, handle, q, lam):
                 g = plan.block_index(i, j, k)
                 same(fused[g], ref[i][j][k])
                 same(unfused[g], ref[i][j][k])
+                same(plain[g], ref[i][j][k])
+
+
+def test_plan_autotune_keeps_bits(tsg, handle):
+    shapes = gen.er_batch_shapes(16, seed=999, log2_lo=8, log2_hi=12)
+    pairs = [(gen.er(n, n, min(d, n), 2000 + 2 * t), gen.er(n, n, min(d, n), 2001 + 2 * t))
+             for t, (n, d) in enumerate(shapes)]
+    As = [tsg.DeviceCSR.from_host(a) for a, _ in pairs]
+    Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
+    plan = tsg.Plan(As, Bs)
+    t = plan.autotune()
+    assert 1 <= t.num_bins <= 12 and 1 <= t.warps_per_block <= 16
+    Cs = plan.execute()
+    Cs = plan.execute()
+    torch.cuda.synchronize()
+    for (a, b), C in zip(pairs, Cs):
+        same(C, oracle.spgemm(a, b)[0])
+    n0 = plan.launch_count()
+    plan.execute()
+    n1 = plan.launch_count()
+    plan.execute()
+    torch.cuda.synchronize()
+    # every replay launches the same captured kernels
+    assert n1 > n0 and plan.launch_count() - n1 == n1 - n0
+    plan.close()
