@@ -959,6 +959,7 @@ struct spgemm_plan {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> exec_key;
     int64_t graph_kernels = 0;  // kernels in the captured graph
+    cudaStream_t capture = nullptr;  // private stream the graph is captured on
 };
 
 namespace {
@@ -1073,13 +1074,16 @@ spgemm_status spgemm_plan_execute(spgemm_plan* p, const spgemm_csr_out* C, int32
     plan_drop_graph(p);
     const bool timing = p->h->timing;
     p->h->timing = false;
-    TSG_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    // (the caller's stream may be the legacy default stream, which cannot be
+    // captured: capture on the plan's own stream, replay on the caller's)
+    if (!p->capture) TSG_CHECK(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
+    TSG_CHECK(cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal));
     const int64_t before = p->h->launches;
-    spgemm_status rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);
+    spgemm_status rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, p->capture);
     p->graph_kernels = p->h->launches - before;
     p->h->launches = before;  // captured, not launched
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cudaError_t e = cudaStreamEndCapture(p->capture, &graph);
     p->h->timing = timing;
     if (rc != SPGEMM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -1202,6 +1206,7 @@ spgemm_status spgemm_plan_destroy(spgemm_plan* p) {
     if (!p) return SPGEMM_OK;
     plan_drop_graph(p);
     spgemm_destroy(p->h);
+    if (p->capture) cudaStreamDestroy(p->capture);
     delete p;
     return SPGEMM_OK;
 }
