@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
 }
 
 cudaError_t launch_scan(const int* counts, long long n, long long* bsum, long long* ex, cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(ex, 0, sizeof(long long), s);  // ex[0] = 0
     const long long nb = scan_blocks(n);
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, n, bsum);
     k_scan_top<<<1, kScanThreads, 0, s>>>(bsum, nb);
