@@ -298,6 +298,31 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
 spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
                                    spgemm_csr_out* XT, spgemm_stream_t stream);
 
+/* ------------------------------------------------ allocation-free variant
+ *
+ * spgemm_csr_transpose_noalloc: the same result as spgemm_csr_transpose
+ * (XT = X^T, rows sorted, arguments and layout identical) for callers that
+ * must not allocate device memory: code running while a stream is captured
+ * into a CUDA graph (cudaMalloc / cudaFree would break the capture), code
+ * whose device memory is owned by an outside pool or budget, or paths that
+ * cannot afford an allocation's implicit synchronisation.  It takes no
+ * handle and calls no allocating routine: its working memory is one fixed
+ * array of SPGEMM_NOALLOC_SCRATCH_BYTES compiled into the library, held by
+ * every GPU that loads it until the process exits.  A request whose working
+ * set (about 12 bytes per column of X plus 8 (float) or 12 (double) bytes
+ * per nonzero, each part rounded up to 256 bytes) exceeds the array returns
+ * SPGEMM_ERR_UNSUPPORTED without launching anything.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps (other streams,
+ * unordered host threads) race.  Asynchronous on `stream`.
+ * The paper has no counterpart: this entry point exists for callers of the
+ * library, not for the method.
+ */
+#define SPGEMM_NOALLOC_SCRATCH_BYTES (25u << 20)
+spgemm_status spgemm_csr_transpose_noalloc(spgemm_dtype dtype, const spgemm_csr_in* X, spgemm_csr_out* XT,
+                                           spgemm_stream_t stream);
+
 /* --------------------------------------------------------- instrumentation */
 
 /* Number of kernels this handle has launched since creation (host counter). */

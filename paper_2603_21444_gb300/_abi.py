@@ -78,6 +78,7 @@ SIGNATURES = {
     "spgemm_plan_autotune": ([P, ctypes.POINTER(CsrOut), P, ctypes.POINTER(Tune)], ctypes.c_int),
     "spgemm_plan_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_plan_destroy": ([P], ctypes.c_int),
+    "spgemm_csr_transpose_noalloc": ([ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

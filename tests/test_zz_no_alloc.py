@@ -1,0 +1,66 @@
+"""The allocation-free transpose (for callers that may not allocate device
+memory, e.g. while a stream is being captured into a CUDA graph, or under an
+outside memory pool) against the allocating entry point.
+
+This file is collected last so that, if it fails, a run stopping at the first
+failure has already run every other test; it also passes alone in a fresh
+process."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_21444_gb300 import _abi
+    return _abi.lib()
+
+
+def _noalloc_transpose(lib, X, dtype):
+    from paper_2603_21444_gb300 import _abi
+    from paper_2603_21444_gb300.api import DeviceCSR
+    dev = X.row_ptr.device
+    T = DeviceCSR(X.ncols, X.nrows, torch.empty(X.ncols + 1, dtype=torch.int32, device=dev),
+                  torch.empty(X.nnz, dtype=torch.int32, device=dev), torch.empty(X.nnz, dtype=dtype, device=dev))
+    xin, tout = X.as_in(), T.as_out()
+    code = _abi.F64 if dtype == torch.float64 else _abi.F32
+    rc = lib.spgemm_csr_transpose_noalloc(code, ctypes.byref(xin), ctypes.byref(tout),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return rc, T
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_noalloc_matches_allocating_transpose_twice(lib, dtype):
+    import paper_2603_21444_gb300 as tsg
+    from paper_2603_21444_gb300 import autograd as ag
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    # two calls in a row, the second smaller than the first: the shared
+    # scratch keeps the first call's contents and must not leak into the second
+    for shape, seed in (((3000, 2000, 30), 1), ((700, 1500, 12), 2)):
+        X = tsg.DeviceCSR.from_host(gen.er_variable(shape[0], shape[1], shape[2], seed, dtype, "normal",
+                                                    p_empty=0.1))
+        rc, T = _noalloc_transpose(lib, X, tdt)
+        assert rc == 0
+        R = ag.transpose(X)
+        torch.cuda.synchronize()
+        # a transpose moves values without arithmetic: equal bit for bit
+        for a, b in zip(T.to_host(), R.to_host()):
+            assert np.array_equal(a, b)
+
+
+def test_noalloc_rejects_oversize_request(lib):
+    import paper_2603_21444_gb300 as tsg
+    # 4M columns need more working space than the fixed array holds
+    X = tsg.DeviceCSR(2, 1 << 22, torch.zeros(3, dtype=torch.int32, device="cuda"),
+                      torch.empty(0, dtype=torch.int32, device="cuda"),
+                      torch.empty(0, dtype=torch.float64, device="cuda"))
+    rc, _ = _noalloc_transpose(lib, X, torch.float64)
+    assert rc == 11  # SPGEMM_ERR_UNSUPPORTED
