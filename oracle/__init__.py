@@ -21,6 +21,9 @@ Contents (each function names the passage of the paper it follows):
                    (Alg. 1 + Alg. 2 with the allgathered B_{r'j} used whole).
 * ``backward``     gradients of L(C) on fixed patterns (chain rule on Sec. 2's
                    definition): dA = (G B^T) on pat(A), dB = (A^T G) on pat(B).
+* ``mcl_step``     one Markov-clustering iteration (Sec. 5.6) on the transposed
+                   column-stochastic matrix: expansion, inflation, pruning,
+                   top-k selection, renormalisation.
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -82,6 +85,8 @@ def _load():
             f.restype = ctypes.c_int
         lib.oracle_spgemm_backward_f64.argtypes = [I64, I64] + [P] * 11
         lib.oracle_spgemm_backward_f64.restype = ctypes.c_int
+        lib.oracle_spgemm_fill_f32p64.argtypes = [I64] + [P] * 9
+        lib.oracle_spgemm_fill_f32p64.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -324,3 +329,85 @@ def transpose(A: CSR) -> CSR:
     rp = np.zeros(A.ncols + 1, dtype=np.int64)
     np.cumsum(counts, out=rp[1:])
     return CSR(A.ncols, A.nrows, rp, rows[order].astype(np.int32), A.val[order])
+
+
+# ---------------------------------------------------------- Markov clustering
+
+def spgemm_f32p64(A: CSR, B: CSR) -> CSR:
+    """C = A B for float inputs: each product rounded to float, the products
+    of an entry added in double in list order (values returned as float64)."""
+    lib = _load()
+    arp, acol = _canon(A)
+    brp, bcol = _canon(B)
+    aval = np.ascontiguousarray(A.val, dtype=np.float32)
+    bval = np.ascontiguousarray(B.val, dtype=np.float32)
+    m = A.nrows
+    counts = np.zeros(m, dtype=np.int64)
+    if m and lib.oracle_spgemm_counts(m, _p(arp), _p(acol), _p(brp), _p(bcol), _p(counts)):
+        raise MemoryError("oracle scratch allocation failed")
+    crp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=crp[1:])
+    ccol = np.zeros(int(crp[-1]), dtype=np.int32)
+    cval = np.zeros(int(crp[-1]), dtype=np.float64)
+    if m and lib.oracle_spgemm_fill_f32p64(m, _p(arp), _p(acol), _p(aval), _p(brp), _p(bcol), _p(bval), _p(crp),
+                                           _p(ccol), _p(cval)):
+        raise RuntimeError("oracle fill failed")
+    return CSR(m, B.ncols, crp, ccol, cval)
+
+
+def mcl_select(cols: np.ndarray, e: np.ndarray, inflation: float = 2.0, prune: float = 1e-4, topk: int = 1000):
+    """Inflation, pruning, top-k and renormalisation of one expanded row
+    (Sec. 5.6; the row is a column of the Markov matrix).  All decisions in
+    double:
+      w_j = e_j ** r (r = 2: e_j * e_j), v_j = w_j / sum_j w_j
+      keep v_j >= prune; if nothing is kept, keep the largest v_j
+      if more than topk are kept, keep the topk largest
+      ties (equal v) go to the smaller column index
+      out_j = float(v_j / sum of kept v)
+    Returns (kept columns ascending, float32 values, dict of the cuts)."""
+    if cols.size == 0:
+        return cols, np.zeros(0, dtype=np.float32), {}
+    w = e * e if inflation == 2.0 else np.power(e, inflation)
+    v = w / w.sum()
+    keep = v >= prune
+    cuts = {"prune": prune}
+    if not keep.any():
+        order = np.lexsort((cols, -v))
+        keep = np.zeros_like(keep)
+        keep[order[0]] = True
+    elif keep.sum() > topk:
+        idx = np.nonzero(keep)[0]
+        order = idx[np.lexsort((cols[idx], -v[idx]))]
+        keep = np.zeros_like(keep)
+        keep[order[:topk]] = True
+        cuts["topk_value"] = float(v[order[topk - 1]])
+    t = v[keep].sum()
+    return cols[keep], (v[keep] / t).astype(np.float32), dict(cuts, v=v, cols=cols)
+
+
+def mcl_step(Mt: CSR, inflation: float = 2.0, prune: float = 1e-4, topk: int = 1000,
+             rows: np.ndarray | None = None):
+    """One MCL iteration on the transposed stochastic matrix Mt (row r of Mt
+    is column r of M): the expansion (M M)^T = Mt Mt, then ``mcl_select`` per
+    row.  With ``rows``, only those rows are formed (returned as a dict
+    row -> (cols, vals, cuts)); otherwise the whole next iterate as CSR."""
+    sel = np.arange(Mt.nrows) if rows is None else np.asarray(rows)
+    lens = Mt.row_lengths()[sel]
+    rp = np.zeros(sel.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(Mt.rowptr[r], Mt.rowptr[r + 1]) for r in sel]) if sel.size else \
+        np.zeros(0, dtype=np.int64)
+    sub = CSR(sel.size, Mt.ncols, rp, Mt.col[idx], Mt.val[idx])
+    E = spgemm_f32p64(sub, Mt)
+    out = {}
+    for t, r in enumerate(sel):
+        a, b = E.rowptr[t], E.rowptr[t + 1]
+        out[int(r)] = mcl_select(E.col[a:b], E.val[a:b], inflation, prune, topk)
+    if rows is not None:
+        return out
+    counts = np.array([out[r][0].size for r in range(Mt.nrows)], dtype=np.int64)
+    nrp = np.zeros(Mt.nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=nrp[1:])
+    col = np.concatenate([out[r][0] for r in range(Mt.nrows)]).astype(np.int32)
+    val = np.concatenate([out[r][1] for r in range(Mt.nrows)]).astype(np.float32)
+    return CSR(Mt.nrows, Mt.ncols, nrp, col, val)

@@ -315,3 +315,58 @@ int oracle_spgemm_backward_f64(int64_t m, int64_t kdim,
     }
     return err;
 }
+
+/* ------------------------------------------- mixed precision (float in)
+ *
+ * Float inputs, each product rounded to float (as the float path does), the
+ * products of an entry added in double in list order.  Used by the Markov
+ * clustering expansion, whose decisions (prune, top-k) are taken in double.
+ */
+int oracle_spgemm_fill_f32p64(int64_t m, const int64_t* arp, const int32_t* acol, const float* aval,
+                              const int64_t* brp, const int32_t* bcol, const float* bval,
+                              const int64_t* crp, int32_t* ccol, double* cval) {
+    int err = 0;
+    #pragma omp parallel
+    {
+        okey* key = NULL; double* prod = NULL;
+        int64_t cap = 0;
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t u = 0;
+            for (int64_t e = arp[i]; e < arp[i + 1]; ++e) u += brp[acol[e] + 1] - brp[acol[e]];
+            if (u > cap) {
+                free(key); free(prod);
+                cap = u;
+                key = (okey*)malloc((size_t)cap * sizeof(okey));
+                prod = (double*)malloc((size_t)cap * sizeof(double));
+                if (!key || !prod) { cap = 0; err = 1; continue; }
+            }
+            int64_t n = 0;
+            for (int64_t e = arp[i]; e < arp[i + 1]; ++e) {
+                int32_t k = acol[e];
+                float a = aval[e];
+                for (int64_t f = brp[k]; f < brp[k + 1]; ++f) {
+                    float p = a * bval[f];
+                    key[n].col = bcol[f];
+                    key[n].seq = n;
+                    prod[n] = (double)p;
+                    ++n;
+                }
+            }
+            qsort(key, (size_t)n, sizeof(okey), okey_cmp);
+            int64_t out = crp[i];
+            for (int64_t t = 0; t < n;) {
+                int32_t j = key[t].col;
+                double s = prod[key[t].seq];
+                int64_t r = t + 1;
+                while (r < n && key[r].col == j) { s = s + prod[key[r].seq]; ++r; }
+                if (out >= crp[i + 1]) { err = 2; break; }
+                ccol[out] = j; cval[out] = s; ++out;
+                t = r;
+            }
+            if (out != crp[i + 1]) err = 2;
+        }
+        free(key); free(prod);
+    }
+    return err;
+}
