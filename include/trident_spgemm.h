@@ -298,6 +298,38 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
 spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
                                    spgemm_csr_out* XT, spgemm_stream_t stream);
 
+/* ------------------------------------------- Markov clustering (Sec. 5.6)
+ *
+ * One iteration of Markov clustering with the expansion step done by this
+ * library's product, fused with the column operations.  The column-
+ * stochastic n x n matrix M is passed TRANSPOSED (Mt: row r = column r of
+ * M, float values), so that (M M)^T = Mt Mt and every column operation is
+ * row-local.  Per row r of the expansion E = Mt Mt:
+ *   e_j accumulated in double from float products a * b (each rounded to
+ *   float);  w_j = e_j^inflation (inflation 2: e_j * e_j);  v_j = w_j / sum w;
+ *   keep v_j >= prune (none kept: keep the largest v_j);  more than topk kept:
+ *   keep the topk largest v_j;  equal v_j: the smaller column first;
+ *   out_j = (float)(v_j / sum of kept v_j).
+ * All keep/drop decisions are taken in double.  1 <= topk <= 1024.
+ * spgemm_mcl_expand: computes the next iterate's row_ptr (device, n+1 int32,
+ * caller-allocated) and *out_nnz (host), keeping the entries in the handle's
+ * workspace; synchronises.  spgemm_mcl_collect: copies them into out->col_idx
+ * / out->val (caller-allocated, out_nnz each; out->row_ptr from expand),
+ * asynchronous.  No other call on the handle may come between the two.
+ * The full expansion E is never stored: a row's kept entries (at most
+ * min(products of the row, topk)) are all that is written.
+ */
+typedef struct {
+    double inflation;  /* r of the inflation step (2) */
+    double prune;      /* drop v_j below this (1e-4) */
+    int32_t topk;      /* keep at most this many per row (1000) */
+    int32_t reserved;  /* 0 */
+} spgemm_mcl_params;
+
+spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const spgemm_mcl_params* prm,
+                                int32_t* out_row_ptr, int64_t* out_nnz, spgemm_stream_t stream);
+spgemm_status spgemm_mcl_collect(spgemm_handle* h, spgemm_csr_out* out, spgemm_stream_t stream);
+
 /* ------------------------------------------------ allocation-free variant
  *
  * spgemm_csr_transpose_noalloc: the same result as spgemm_csr_transpose

@@ -41,6 +41,11 @@ class CsrOut(ctypes.Structure):
                 ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class MclParams(ctypes.Structure):
+    _fields_ = [("inflation", ctypes.c_double), ("prune", ctypes.c_double), ("topk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class Tune(ctypes.Structure):
     _fields_ = [("num_bins", ctypes.c_int32), ("bin_upper", ctypes.c_int32 * MAX_BINS),
                 ("bin_kernel", ctypes.c_int32 * MAX_BINS), ("accumulator", ctypes.c_int32),
@@ -79,6 +84,8 @@ SIGNATURES = {
     "spgemm_plan_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_plan_destroy": ([P], ctypes.c_int),
     "spgemm_csr_transpose_noalloc": ([ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
+    "spgemm_mcl_expand": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(MclParams), P, I64P, P], ctypes.c_int),
+    "spgemm_mcl_collect": ([P, ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

@@ -443,3 +443,25 @@ class TridentPlan:
                      for t in range(self.group_ptr[g], self.group_ptr[g + 1])]
             out.append(merge(parts, self.h, stream))
         return out
+
+
+# ------------------------------------------------------- Markov clustering
+
+def mcl_step(Mt: DeviceCSR, inflation: float = 2.0, prune: float = 1e-4, topk: int = 1000,
+             handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """One Markov-clustering iteration (Sec. 5.6) on the transposed
+    column-stochastic matrix: expansion fused with inflation, pruning, top-k
+    and renormalisation (``spgemm_mcl_expand`` / ``spgemm_mcl_collect``)."""
+    h = handle or default_handle()
+    prm = _abi.MclParams(float(inflation), float(prune), int(topk), 0)
+    dev = Mt.row_ptr.device
+    rp = torch.empty(Mt.nrows + 1, dtype=torch.int32, device=dev)
+    nnz = ctypes.c_int64()
+    mi = Mt.as_in()
+    check(_abi.lib().spgemm_mcl_expand(h.ptr, ctypes.byref(mi), ctypes.byref(prm), ctypes.c_void_p(rp.data_ptr()),
+                                       ctypes.byref(nnz), _stream(stream)), "spgemm_mcl_expand")
+    out = DeviceCSR(Mt.nrows, Mt.ncols, rp, torch.empty(nnz.value, dtype=torch.int32, device=dev),
+                    torch.empty(nnz.value, dtype=torch.float32, device=dev))
+    oo = out.as_out()
+    check(_abi.lib().spgemm_mcl_collect(h.ptr, ctypes.byref(oo), _stream(stream)), "spgemm_mcl_collect")
+    return out

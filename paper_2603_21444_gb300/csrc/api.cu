@@ -53,6 +53,10 @@ struct spgemm_handle {
     DevBuf dense;
     DevBuf status;  // the device status word latched by kernels
     DevBuf tr;      // transpose work and the A^T of the deterministic backward
+    DevBuf mcl;     // Markov clustering: bounds, offsets, kept entries
+    DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
+    int mcl_n = -1;
+    long long mcl_total = 0;
     void* pinned = nullptr;
     size_t pinned_n = 0;
     // plan cache (bin lists of the last sizing call)
@@ -558,6 +562,8 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->dense.p) cudaFree(h->dense.p);
     if (h->status.p) cudaFree(h->status.p);
     if (h->tr.p) cudaFree(h->tr.p);
+    if (h->mcl.p) cudaFree(h->mcl.p);
+    if (h->mcl_acc.p) cudaFree(h->mcl_acc.p);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -890,6 +896,139 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
     PhaseScope ps(h, 6, st);
     TSG_CHECK(launch_backward(dtype, a, h->sms, st));
     h->launches += 2;
+    return SPGEMM_OK;
+}
+
+namespace {
+
+struct MclLayout {
+    size_t ub, ub_off, bsum, kept, ex, ctr, tmp_col, tmp_val, bytes;
+};
+
+MclLayout mcl_layout(long long n, long long total) {
+    MclLayout L;
+    L.ub = 0;
+    L.ub_off = L.ub + align16(4 * std::max(n, 1ll));
+    L.bsum = L.ub_off + align16(8 * (n + 1));
+    L.kept = L.bsum + align16(8 * scan_blocks(std::max(n, 1ll)));
+    L.ex = L.kept + align16(4 * std::max(n, 1ll));
+    L.ctr = L.ex + align16(8 * (n + 1));
+    L.tmp_col = L.ctr + 16;
+    L.tmp_val = L.tmp_col + align16(4 * std::max(total, 1ll));
+    L.bytes = L.tmp_val + align16(4 * std::max(total, 1ll));
+    return L;
+}
+
+}  // namespace
+
+spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const spgemm_mcl_params* prm,
+                                int32_t* out_row_ptr, int64_t* out_nnz, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(Mt, true) || !prm || !out_row_ptr || !out_nnz) return SPGEMM_ERR_INVALID_ARG;
+    if (Mt->nrows != Mt->ncols) return SPGEMM_ERR_SHAPE;
+    if (prm->topk < 1 || prm->topk > 1024 || !(prm->inflation > 0.0) || !(prm->prune >= 0.0))
+        return SPGEMM_ERR_INVALID_ARG;
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    h->mcl_n = -1;
+    const long long n = Mt->nrows;
+    if (n == 0) {
+        TSG_CHECK(cudaMemsetAsync(out_row_ptr, 0, sizeof(int), st));
+        *out_nnz = 0;
+        h->mcl_n = 0;
+        h->mcl_total = 0;
+        return SPGEMM_OK;
+    }
+    if ((long long)prm->topk * n > (1ll << 31) - 1) return SPGEMM_ERR_INDEX_OVERFLOW;
+    TSG_TRY(grow(h->status, 16, st, true));
+    TSG_TRY(grow_pinned(h, 64));
+    long long* p_ll = static_cast<long long*>(h->pinned);
+    // 1. per-row bound min(products, topk) and its exclusive sums
+    MclLayout L0 = mcl_layout(n, 1);
+    TSG_TRY(grow(h->mcl, L0.bytes));
+    char* b = static_cast<char*>(h->mcl.p);
+    PhaseScope ps(h, 7, st);
+    TSG_CHECK(launch_mcl_bounds(Mt->row_ptr, Mt->col_idx, (int)n, prm->topk, reinterpret_cast<int*>(b + L0.ub), st));
+    TSG_CHECK(launch_scan(reinterpret_cast<int*>(b + L0.ub), n, reinterpret_cast<long long*>(b + L0.bsum),
+                          reinterpret_cast<long long*>(b + L0.ub_off), st));
+    TSG_CHECK(cudaMemcpyAsync(p_ll, b + L0.ub_off + 8 * n, 8, cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(cudaStreamSynchronize(st));
+    const long long total = p_ll[0];
+    MclLayout L = mcl_layout(n, total);
+    if (h->mcl.n < L.bytes) {
+        // keep the bounds already computed while growing
+        DevBuf nb;
+        TSG_TRY(grow(nb, L.bytes));
+        TSG_CHECK(cudaMemcpyAsync(nb.p, h->mcl.p, L0.tmp_col, cudaMemcpyDeviceToDevice, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        cudaFree(h->mcl.p);
+        h->mcl = nb;
+    }
+    b = static_cast<char*>(h->mcl.p);
+    // 2. per-block accumulators: dense doubles, touched list, bitmap
+    const long long stride = (n + 31) & ~31ll;
+    const long long bm_words = stride / 32;
+    const int slots = (int)std::min<long long>(n, (long long)h->sms * 4);
+    const size_t per = 8 * stride + 4 * stride + 4 * bm_words;
+    if (h->mcl_acc.n < per * slots) TSG_TRY(grow(h->mcl_acc, per * slots, st, true));
+    char* acc = static_cast<char*>(h->mcl_acc.p);
+    TSG_CHECK(cudaMemsetAsync(b + L.kept, 0, 4 * n, st));
+    TSG_CHECK(cudaMemsetAsync(b + L.ctr, 0, 16, st));
+    MclLaunch ml;
+    ml.n = (int)n;
+    ml.rp = Mt->row_ptr;
+    ml.col = Mt->col_idx;
+    ml.val = static_cast<const float*>(Mt->val);
+    ml.ub_off = reinterpret_cast<const long long*>(b + L.ub_off);
+    ml.tmp_col = reinterpret_cast<int*>(b + L.tmp_col);
+    ml.tmp_val = reinterpret_cast<float*>(b + L.tmp_val);
+    ml.kept = reinterpret_cast<int*>(b + L.kept);
+    ml.dense = reinterpret_cast<double*>(acc);
+    ml.touched = reinterpret_cast<int*>(acc + 8 * stride * slots);
+    ml.bitmap = reinterpret_cast<unsigned*>(acc + 12 * stride * slots);
+    ml.stride = stride;
+    ml.bm_words = bm_words;
+    ml.row_counter = reinterpret_cast<int*>(b + L.ctr);
+    ml.inflation = prm->inflation;
+    ml.prune = prm->prune;
+    ml.topk = prm->topk;
+    ml.status = static_cast<unsigned*>(h->status.p);
+    TSG_CHECK(launch_mcl_rows(ml, slots, st));
+    // 3. row pointers of the next iterate
+    TSG_CHECK(launch_scan(reinterpret_cast<int*>(b + L.kept), n, reinterpret_cast<long long*>(b + L.bsum),
+                          reinterpret_cast<long long*>(b + L.ex), st));
+    TSG_CHECK(launch_ll_to_int(reinterpret_cast<long long*>(b + L.ex), n + 1, out_row_ptr, st));
+    h->launches += 9;
+    unsigned* p_status = reinterpret_cast<unsigned*>(p_ll + 1);
+    TSG_CHECK(cudaMemcpyAsync(p_ll, b + L.ex + 8 * n, 8, cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(cudaMemcpyAsync(p_status, h->status.p, 4, cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(cudaStreamSynchronize(st));
+    if (*p_status) {
+        TSG_CHECK(cudaMemsetAsync(h->status.p, 0, 4, st));
+        return SPGEMM_ERR_INTERNAL;
+    }
+    *out_nnz = p_ll[0];
+    h->mcl_n = (int)n;
+    h->mcl_total = total;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_mcl_collect(spgemm_handle* h, spgemm_csr_out* out, spgemm_stream_t stream) {
+    if (!h || !out || !out->row_ptr) return SPGEMM_ERR_INVALID_ARG;
+    if (h->mcl_n < 0 || out->nrows != h->mcl_n || out->ncols != h->mcl_n) return SPGEMM_ERR_INVALID_ARG;
+    if (h->mcl_n == 0) return SPGEMM_OK;
+    if (!out->col_idx || !out->val) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    const MclLayout L = mcl_layout(h->mcl_n, h->mcl_total);
+    char* b = static_cast<char*>(h->mcl.p);
+    PhaseScope ps(h, 7, st);
+    TSG_CHECK(launch_mcl_collect(h->mcl_n, reinterpret_cast<const long long*>(b + L.ub_off),
+                                 reinterpret_cast<const int*>(b + L.tmp_col), reinterpret_cast<const float*>(b + L.tmp_val),
+                                 out->row_ptr, out->col_idx, static_cast<float*>(out->val), h->sms, st));
+    ++h->launches;
     return SPGEMM_OK;
 }
 

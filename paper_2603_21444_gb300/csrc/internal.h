@@ -94,6 +94,32 @@ cudaError_t launch_transpose(int dtype, const int* rp, const int* col, const voi
                              long long nnz, int* trp, int* tcol, void* tval, int* work, void* workv, long long* bsum,
                              long long* ex, int sms, cudaStream_t s);
 
+// Markov-clustering iteration (mcl.cu)
+struct MclLaunch {
+    int n;
+    const int* rp;
+    const int* col;
+    const float* val;
+    const long long* ub_off;
+    int* tmp_col;
+    float* tmp_val;
+    int* kept;
+    double* dense;
+    unsigned* bitmap;
+    int* touched;
+    long long stride;
+    long long bm_words;
+    int* row_counter;
+    double inflation;
+    double prune;
+    int topk;
+    unsigned* status;
+};
+cudaError_t launch_mcl_bounds(const int* rp, const int* col, int n, int topk, int* ub, cudaStream_t s);
+cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s);
+cudaError_t launch_mcl_collect(int n, const long long* ub_off, const int* tmp_col, const float* tmp_val,
+                               const int* orp, int* ocol, float* oval, int sms, cudaStream_t s);
+
 // trident partition (partition.cu)
 cudaError_t launch_split_count(const int* rp, const int* col, int nrows, const int* cb, int ncp, int* counts,
                                cudaStream_t s);
