@@ -112,8 +112,10 @@ typedef struct {
     int32_t bin_upper[SPGEMM_MAX_BINS];    /* increasing product-count bounds */
     int32_t bin_kernel[SPGEMM_MAX_BINS];   /* variant per bin */
     int32_t accumulator;                   /* SPGEMM_ACC_SORT */
-    int32_t warps_per_block;               /* blocks of warp-team variants: 1..16 */
+    int32_t warps_per_block;               /* blocks of warp-team variants: 1..32 (clamped per
+                                              variant to what its shared memory allows) */
     int32_t validate;                      /* nonzero: check inputs on the device */
+    int32_t sym_warps_per_block;           /* symbolic pass; 0 = warps_per_block */
 } spgemm_tune;
 
 typedef struct spgemm_handle spgemm_handle;

@@ -49,7 +49,8 @@ class MclParams(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("num_bins", ctypes.c_int32), ("bin_upper", ctypes.c_int32 * MAX_BINS),
                 ("bin_kernel", ctypes.c_int32 * MAX_BINS), ("accumulator", ctypes.c_int32),
-                ("warps_per_block", ctypes.c_int32), ("validate", ctypes.c_int32)]
+                ("warps_per_block", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("sym_warps_per_block", ctypes.c_int32)]
 
 
 # name -> (argtypes, restype); every exported symbol of the header

@@ -140,14 +140,16 @@ void default_tune(spgemm_tune* t) {
         t->bin_kernel[b] = b;
     }
     t->accumulator = SPGEMM_ACC_SORT;
-    t->warps_per_block = 8;
+    t->warps_per_block = 16;
     t->validate = 0;
+    t->sym_warps_per_block = 8;
 }
 
 spgemm_status check_tune(const spgemm_tune* t) {
     if (t->num_bins < 1 || t->num_bins > SPGEMM_MAX_BINS) return SPGEMM_ERR_INVALID_ARG;
     if (t->accumulator != SPGEMM_ACC_SORT) return SPGEMM_ERR_INVALID_ARG;
-    if (t->warps_per_block < 1 || t->warps_per_block > 16) return SPGEMM_ERR_INVALID_ARG;
+    if (t->warps_per_block < 1 || t->warps_per_block > 32) return SPGEMM_ERR_INVALID_ARG;
+    if (t->sym_warps_per_block < 0 || t->sym_warps_per_block > 32) return SPGEMM_ERR_INVALID_ARG;
     for (int b = 0; b < t->num_bins; ++b) {
         const int v = t->bin_kernel[b];
         if (v < 0 || v >= kNumVariants) return SPGEMM_ERR_INVALID_ARG;
@@ -212,14 +214,19 @@ struct PhaseScope {
     }
 };
 
-void occupancy(spgemm_handle* h, int wpb) {
-    if (h->occ_wpb == wpb) return;
+// warps per block of variant v for the requested setting (clamped to what
+// the variant's launch bound and shared memory allow)
+int sym_wpb(int v, int wpb) { return std::min(wpb, warp_variant_max_wpb(v, sym_smem_bytes(v, 1))); }
+int num_wpb(int v, int dtype, int wpb) { return std::min(wpb, warp_variant_max_wpb(v, num_smem_bytes(v, dtype, 1))); }
+
+void occupancy(spgemm_handle* h, int wpb, int swpb) {
+    if (h->occ_wpb == wpb * 64 + swpb) return;
     for (int v = 0; v < kNumVariants; ++v) {
-        h->occ_sym[v] = std::max(1, sym_blocks_per_sm(v, wpb));
-        h->occ_num[0][v] = std::max(1, num_blocks_per_sm(v, 0, wpb));
-        h->occ_num[1][v] = std::max(1, num_blocks_per_sm(v, 1, wpb));
+        h->occ_sym[v] = std::max(1, sym_blocks_per_sm(v, sym_wpb(v, swpb)));
+        h->occ_num[0][v] = std::max(1, num_blocks_per_sm(v, 0, num_wpb(v, 0, wpb)));
+        h->occ_num[1][v] = std::max(1, num_blocks_per_sm(v, 1, num_wpb(v, 1, wpb)));
     }
-    h->occ_wpb = wpb;
+    h->occ_wpb = wpb * 64 + swpb;
 }
 
 int teams_per_block(int v, int wpb) { return variant_team(v) == 32 ? wpb : 1; }
@@ -385,8 +392,9 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         h->launches += 3;
     }
 
-    occupancy(h, tune.warps_per_block);
     const int wpb = tune.warps_per_block;
+    const int swpb = tune.sym_warps_per_block > 0 ? tune.sym_warps_per_block : wpb;
+    occupancy(h, wpb, swpb);
     RowLaunchArgs la;
     la.inst = d_inst;
     la.groups = d_groups;
@@ -405,7 +413,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             for (int b = 0; b < nb; ++b) {
                 const int v = tune.bin_kernel[b];
                 la.bin = b;
-                TSG_CHECK(launch_sym_rows(v, la, h->sms * h->occ_sym[v], wpb, st));
+                TSG_CHECK(launch_sym_rows(v, la, h->sms * h->occ_sym[v], sym_wpb(v, swpb), st));
                 ++h->launches;
             }
         }
@@ -470,11 +478,12 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         for (int b = 0; b < nb; ++b) {
             if (hist[b] == 0) continue;
             const int v = tune.bin_kernel[b];
-            const int tpb = teams_per_block(v, wpb);
+            const int wv = num_wpb(v, dtype, wpb);
+            const int tpb = teams_per_block(v, wv);
             const long long need = (hist[b] + tpb - 1) / tpb;
             const int blocks = (int)std::min<long long>(need, (long long)h->sms * h->occ_num[dtype][v]);
             la.bin = b;
-            TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wpb, st));
+            TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wv, st));
             ++h->launches;
         }
     }
@@ -1271,7 +1280,7 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
     std::vector<spgemm_tune> cand;
     spgemm_tune base;
     default_tune(&base);
-    for (int wpb : {8, 4, 16}) {
+    for (int wpb : {16, 8, 32}) {
         spgemm_tune t = base;
         t.warps_per_block = wpb;
         cand.push_back(t);

@@ -191,7 +191,7 @@ __device__ __forceinline__ void sym_row(const RowArgs& a, int unit, char* sm) {
 }
 
 template <int TEAM, int PER>
-__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, (TEAM == 32 && PER <= 8) ? 2 : 1) k_sym_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1) k_sym_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -610,13 +610,20 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     }
     __syncwarp();
 
+    // the meta is dead from here on: the remaining arrays never alias
+    int* __restrict__ xcnt = cnt;
+    int* __restrict__ xcol = ocol;
+    T* __restrict__ xval = oval;
+    unsigned short* __restrict__ xp = op;
+    unsigned char* __restrict__ xinst = oinst;
+    unsigned short* __restrict__ xwl = wl;
     // ---- bucket starts: exclusive scan in rounds of 32 x 4 counters
     {
         int base = 0;
         for (int i0 = 0; i0 < NB; i0 += 128) {
             const int i = i0 + 4 * lane;
             int4 v = make_int4(0, 0, 0, 0);
-            if (i < NB) v = *reinterpret_cast<const int4*>(cnt + i);
+            if (i < NB) v = *reinterpret_cast<const int4*>(xcnt + i);
             const int loc = v.x + v.y + v.z + v.w;
             int x = loc;
 #pragma unroll
@@ -631,11 +638,11 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
                 o.y = ex; ex += v.y;
                 o.z = ex; ex += v.z;
                 o.w = ex;
-                *reinterpret_cast<int4*>(cnt + i) = o;
+                *reinterpret_cast<int4*>(xcnt + i) = o;
             }
             base += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane == 0) cnt[NB] = u;
+        if (lane == 0) xcnt[NB] = u;
     }
     __syncwarp();
 
@@ -643,51 +650,51 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
 #pragma unroll
     for (int s = 0; s < PER; ++s)
         if (col[s] >= 0) {
-            const int pos = cnt[bk(col[s])] + (hh[s] & 0xffff);
-            ocol[pos] = col[s];
-            oval[pos] = val[s];
+            const int pos = xcnt[bk(col[s])] + (hh[s] & 0xffff);
+            xcol[pos] = col[s];
+            xval[pos] = val[s];
             if (!distinct) {
-                op[pos] = (unsigned short)(lane * PER + s);
-                if (multi) oinst[pos] = (unsigned char)(hh[s] >> 16);
+                xp[pos] = (unsigned short)(lane * PER + s);
+                if (multi) xinst[pos] = (unsigned char)(hh[s] >> 16);
             }
         }
     __syncwarp();
 
     // ---- sort each listed bucket in place: by column, ties by p
     for (int w = lane; w < nwl; w += 32) {
-        const int b = wl[w];
-        const int lo = cnt[b], hi = cnt[b + 1];
+        const int b = xwl[w];
+        const int lo = xcnt[b], hi = xcnt[b + 1];
         if (distinct) {
             for (int i = lo + 1; i < hi; ++i) {
-                const int c = ocol[i];
-                const T v = oval[i];
+                const int c = xcol[i];
+                const T v = xval[i];
                 int j = i - 1;
-                while (j >= lo && ocol[j] > c) {
-                    ocol[j + 1] = ocol[j];
-                    oval[j + 1] = oval[j];
+                while (j >= lo && xcol[j] > c) {
+                    xcol[j + 1] = xcol[j];
+                    xval[j + 1] = xval[j];
                     --j;
                 }
-                ocol[j + 1] = c;
-                oval[j + 1] = v;
+                xcol[j + 1] = c;
+                xval[j + 1] = v;
             }
         } else {
             for (int i = lo + 1; i < hi; ++i) {
-                const int c = ocol[i];
-                const int pp = op[i];
-                const T v = oval[i];
-                const unsigned char ins = multi ? oinst[i] : 0;
+                const int c = xcol[i];
+                const int pp = xp[i];
+                const T v = xval[i];
+                const unsigned char ins = multi ? xinst[i] : 0;
                 int j = i - 1;
-                while (j >= lo && (ocol[j] > c || (ocol[j] == c && op[j] > pp))) {
-                    ocol[j + 1] = ocol[j];
-                    op[j + 1] = op[j];
-                    oval[j + 1] = oval[j];
-                    if (multi) oinst[j + 1] = oinst[j];
+                while (j >= lo && (xcol[j] > c || (xcol[j] == c && xp[j] > pp))) {
+                    xcol[j + 1] = xcol[j];
+                    xp[j + 1] = xp[j];
+                    xval[j + 1] = xval[j];
+                    if (multi) xinst[j + 1] = xinst[j];
                     --j;
                 }
-                ocol[j + 1] = c;
-                op[j + 1] = (unsigned short)pp;
-                oval[j + 1] = v;
-                if (multi) oinst[j + 1] = ins;
+                xcol[j + 1] = c;
+                xp[j + 1] = (unsigned short)pp;
+                xval[j + 1] = v;
+                if (multi) xinst[j + 1] = ins;
             }
         }
     }
@@ -698,8 +705,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     if (distinct) {
         // ---- sorted products are the row: copy out
         for (int q = lane; q < u; q += 32) {
-            ccol[q] = ocol[q];
-            cval[q] = oval[q];
+            ccol[q] = xcol[q];
+            cval[q] = xval[q];
         }
         __syncwarp();
         return;
@@ -710,28 +717,28 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     for (int q0 = 0; q0 < u; q0 += 32) {
         const int q = q0 + lane;
         const bool valid = q < u;
-        const int c = valid ? ocol[q] : -2;
+        const int c = valid ? xcol[q] : -2;
         int prev = __shfl_up_sync(0xffffffffu, c, 1);
         if (lane == 0) prev = carry;
         int next = __shfl_down_sync(0xffffffffu, c, 1);
-        if (lane == 31) next = q + 1 < u ? ocol[q + 1] : -2;
+        if (lane == 31) next = q + 1 < u ? xcol[q + 1] : -2;
         const bool head = valid && c != prev;
         const unsigned hm = __ballot_sync(0xffffffffu, head);
         if (head) {
-            T res = oval[q];
+            T res = xval[q];
             if (next == c) {
                 // several products on this column: add them in p order (in
                 // merge or multi-instance mode each instance's products first)
                 T sub = res, acc = T(0);
                 bool have = false;
-                int ci = multi ? oinst[q] : 0;
-                for (int e = q + 1; e < u && ocol[e] == c; ++e) {
-                    const T v = oval[e];
-                    if (multi && oinst[e] != ci) {
+                int ci = multi ? xinst[q] : 0;
+                for (int e = q + 1; e < u && xcol[e] == c; ++e) {
+                    const T v = xval[e];
+                    if (multi && xinst[e] != ci) {
                         acc = have ? add_rn(acc, sub) : sub;
                         have = true;
                         sub = v;
-                        ci = oinst[e];
+                        ci = xinst[e];
                     } else {
                         sub = add_rn(sub, v);
                     }
@@ -752,7 +759,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
 }
 
 template <int TEAM, int PER, typename T>
-__global__ void __launch_bounds__(TEAM == 32 ? 512 : TEAM, (TEAM == 32 && PER <= 8) ? 2 : 1) k_num_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1) k_num_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];

@@ -4,6 +4,13 @@
 
 namespace tsg {
 
+int warp_variant_max_wpb(int variant, int per_warp_bytes) {
+    if (variant_team(variant) != 32) return 1;
+    const int by_threads = variant_per(variant) <= 8 ? 32 : 16;
+    const int by_smem = (227 * 1024) / per_warp_bytes;
+    return by_smem < by_threads ? by_smem : by_threads;
+}
+
 int sym_smem_bytes(int variant, int wpb) {
     int bytes = 0;
     dispatch_variant(variant, [&](auto S) {
