@@ -125,6 +125,22 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the numeric rows kernel from the committed ncu
+    capture, or None once the kernel sources differ from the captured ones."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "numeric_traffic.json")) as f:
+            d = json.load(f)
+        h = hashlib.sha256()
+        for fn in d["source_files"]:
+            with open(os.path.join(ROOT, fn), "rb") as g:
+                h.update(g.read())
+        return d["dram_bytes_per_launch_full"] if h.hexdigest() == d["source_sha256"] else None
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -255,8 +271,10 @@ def run_native(args):
     num_ms = phase_ms[3] / max(phase_cnt[3], 1)
     sym_ms = phase_ms[1] / max(phase_cnt[1], 1)
     achieved = num_bytes / (num_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_num_rows<32,8,double> (numeric rows)", "achieved": round(achieved, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+    roof = {"bound": "hbm", "kernel": "k_num_rows<32, 8, double> (numeric rows, warp team)",
+            "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": measured_traffic() if args.n_log2 == 20 and args.d == 16 else None,
             "peak_source": peak_kind, "algorithmic_bytes": num_bytes, "launch_ms": round(num_ms, 4)}
     phases = {"analysis_ms": phase_ms[0] / args.steps, "symbolic_rows_ms": sym_ms, "scan_ms": phase_ms[2] / args.steps,
               "numeric_rows_ms": num_ms, "heavy_ms": phase_ms[4] / args.steps,
