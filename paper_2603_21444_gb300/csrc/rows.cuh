@@ -190,6 +190,255 @@ __device__ __forceinline__ void sym_row(const RowArgs& a, int unit, char* sm) {
     Team<TEAM>::sync();
 }
 
+// ------------------------------------------------- coalesced warp gather
+//
+// A warp team's products are read in chunks of 4: lane L takes chunk
+// s*32 + L (s = 0 .. PER/4 - 1), i.e. products [4(s*32+L), 4(s*32+L) + 4), so
+// one warp instruction covers 128 consecutive products.  A chunk that lies in
+// one B row and starts on a 16-byte boundary is read with 16-byte loads;
+// otherwise element by element.  Product slot e of the lane holds product
+// p = 4 (32 (e / 4) + L) + e % 4.
+
+template <int PER>
+__device__ __forceinline__ int chunk_product(int lane, int e) {
+    constexpr int W = PER < 4 ? PER : 4;
+    return W * (32 * (e / W) + lane) + e % W;
+}
+
+template <typename T>
+struct Vec2 {};
+template <>
+struct Vec2<double> {
+    static __device__ __forceinline__ void load4(const double* p, double* out) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+    }
+};
+template <>
+struct Vec2<float> {
+    static __device__ __forceinline__ void load4(const float* p, float* out) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    }
+};
+
+// Owner entry of product p: the last t with m_pre[t] <= p.
+__device__ __forceinline__ int owner_of(const int* m_pre, int nA, int p) {
+    int lo = 0, hi = nA;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (m_pre[mid] <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// col[e] = column of the lane's e-th product (-1 past u); with VALS,
+// val[e] = a_ik * b_kj (merge: b_kj) and ins[e] = its instance.
+template <int PER, bool VALS, typename T>
+__device__ __forceinline__ void gather_chunks(const RowArgs& a, int ib, int nA, int u, const int* m_pre,
+                                              const int* m_bs, const T* m_a, const unsigned char* m_inst, int lane,
+                                              int (&col)[PER], T (&val)[PER], int (&ins)[PER]) {
+    constexpr int W = PER < 4 ? PER : 4;  // chunk width
+#pragma unroll
+    for (int c = 0; c < PER / W; ++c) {
+        const int p0 = W * (32 * c + lane);
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            col[W * c + v] = -1;
+            if (VALS) val[W * c + v] = T(0);
+            ins[W * c + v] = 0;
+        }
+        if (p0 >= u) continue;
+        int t = owner_of(m_pre, nA, p0);
+        int tb = m_pre[t], te = m_pre[t + 1];
+        int ti = m_inst[t];
+        const InstDev* I = a.inst + ib + ti;
+        const int* bcol = I->bcol;
+        const T* bval = reinterpret_cast<const T*>(I->bval);
+        const int f0 = m_bs[t] + (p0 - tb);
+        T av = VALS ? m_a[t] : T(1);
+        if (W == 4 && p0 + 4 <= te && ((reinterpret_cast<uintptr_t>(bcol + f0) & 15) == 0) &&
+            (!VALS || (reinterpret_cast<uintptr_t>(bval + f0) & 15) == 0)) {
+            const int4 cc = __ldg(reinterpret_cast<const int4*>(bcol + f0));
+            col[W * c + 0] = cc.x;
+            col[W * c + (W > 1 ? 1 : 0)] = W > 1 ? cc.y : cc.x;
+            col[W * c + (W > 2 ? 2 : 0)] = W > 2 ? cc.z : cc.x;
+            col[W * c + (W > 3 ? 3 : 0)] = W > 3 ? cc.w : cc.x;
+            if (VALS) {
+                T bv[4];
+                Vec2<T>::load4(bval + f0, bv);
+#pragma unroll
+                for (int v = 0; v < W; ++v) val[W * c + v] = a.merge ? bv[v] : mul_rn(av, bv[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < W; ++v) ins[W * c + v] = ti;
+        } else {
+#pragma unroll
+            for (int v = 0; v < W; ++v) {
+                const int p = p0 + v;
+                if (p < u) {
+                    while (p >= te) {
+                        ++t;
+                        tb = te;
+                        te = m_pre[t + 1];
+                        if (VALS) av = m_a[t];
+                        const int tn = m_inst[t];
+                        if (tn != ti) {
+                            ti = tn;
+                            I = a.inst + ib + ti;
+                            bcol = I->bcol;
+                            bval = reinterpret_cast<const T*>(I->bval);
+                        }
+                    }
+                    const int f = m_bs[t] + (p - tb);
+                    col[W * c + v] = __ldg(bcol + f);
+                    if (VALS) {
+                        const T bv = __ldg(bval + f);
+                        val[W * c + v] = a.merge ? bv : mul_rn(av, bv);
+                    }
+                    ins[W * c + v] = ti;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------ symbolic, warp-team variant
+//
+// Same count as sym_row (first insertions into a shared-memory hash set of
+// 4 pow2ceil(u) slots), arranged for SIMT efficiency: every product makes one
+// insertion attempt at its home slot, all slots of a lane issued together;
+// the products that met a different column there (about one in eight) are
+// compacted into a list and finish their linear probe one per lane.  The
+// meta keeps B-row offsets (4 B) instead of pointers and shares the table's
+// storage while the products are gathered.
+
+template <int CAP>
+struct WSymLayout {
+    static constexpr int MAXA = CAP / 2;
+    static constexpr int TBL = 4 * CAP;
+    static constexpr int table = 0;                                // int[TBL]
+    static constexpr int clist = 4 * TBL;                          // int[CAP] collided columns
+    static constexpr int bytes = (clist + 4 * CAP + 15) & ~15;
+    static constexpr int m_pre = 0;                                // int[MAXA + 1] (aliases table)
+    static constexpr int m_bs = m_pre + 4 * (MAXA + 1);            // int[MAXA]
+    static constexpr int m_inst = m_bs + 4 * MAXA;                 // u8[MAXA]
+    static_assert(m_inst + MAXA <= clist, "meta does not fit its alias region");
+};
+
+template <int PER>
+__device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* sm) {
+    constexpr int CAP = 32 * PER;
+    using L = WSymLayout<CAP>;
+    int* table = reinterpret_cast<int*>(sm + L::table);
+    int* clist = reinterpret_cast<int*>(sm + L::clist);
+    int* m_pre = reinterpret_cast<int*>(sm + L::m_pre);
+    int* m_bs = reinterpret_cast<int*>(sm + L::m_bs);
+    unsigned char* m_inst = reinterpret_cast<unsigned char*>(sm + L::m_inst);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int g = unit_group(a.unit_base, a.ngroups, unit);
+    const GroupDev& G = a.groups[g];
+    const int rho = (int)(unit - a.unit_base[g]);
+    const int ib = G.inst_begin, icount = G.inst_count;
+
+    int nA = 0, u = 0;
+    for (int t = 0; t < icount; ++t) {
+        const InstDev& I = a.inst[ib + t];
+        int a0 = 0, a1 = 1;
+        if (!a.merge) {
+            a0 = __ldg(I.arp + rho);
+            a1 = __ldg(I.arp + rho + 1);
+        }
+        for (int e0 = a0; e0 < a1; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < a1;
+            int len = 0, bs = 0;
+            if (valid) {
+                const int k = a.merge ? rho : __ldg(I.acol + e);
+                bs = __ldg(I.brp + k);
+                len = __ldg(I.brp + k + 1) - bs;
+            }
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int idx = nA + lane;
+            if (valid && idx < L::MAXA) {
+                m_pre[idx] = u + x - len;
+                m_bs[idx] = bs;
+                m_inst[idx] = (unsigned char)t;
+            }
+            nA += min(32, a1 - e0);
+            u += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    if (nA > L::MAXA || u > CAP) {
+        if (lane == 0) {
+            atomicOr(a.status, kStatusInternal);
+            a.counts[unit] = 0;
+        }
+        __syncwarp();
+        return;
+    }
+    if (lane == 0) m_pre[nA] = u;
+    __syncwarp();
+
+    int col[PER];
+    {
+        float unused_val[PER];
+        int unused_ins[PER];
+        gather_chunks<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, lane, col, unused_val,
+                                         unused_ins);
+    }
+    __syncwarp();  // the meta is dead: the table takes its place
+    const int T2 = 4 * pow2ceil(u);
+    const int shift = 32 - (31 - __clz(T2));
+    for (int i = 4 * lane; i < T2; i += 128) *reinterpret_cast<int4*>(table + i) = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+
+    // one attempt per product at its home slot
+    int fresh = 0, ncol = 0;
+    int old[PER];
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        old[s] = -1;
+        if (col[s] >= 0) old[s] = atomicCAS(&table[((unsigned)col[s] * 0x9E3779B1u) >> shift], -1, col[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        const bool hit = col[s] >= 0 && old[s] == -1;
+        const bool clash = col[s] >= 0 && old[s] != -1 && old[s] != col[s];
+        fresh += hit;
+        const unsigned m = __ballot_sync(0xffffffffu, clash);
+        if (clash) clist[ncol + __popc(m & lt)] = col[s];
+        ncol += __popc(m);
+    }
+    __syncwarp();
+    // the collided products continue their probe, one per lane
+    bool overflow = false;
+    for (int w = lane; w < ncol; w += 32) {
+        const int c = clist[w];
+        unsigned h = ((((unsigned)c * 0x9E3779B1u) >> shift) + 1) & (T2 - 1);
+        int probe = 1;
+        for (; probe < T2; ++probe) {
+            const int o = atomicCAS(&table[h], -1, c);
+            if (o == -1) { ++fresh; break; }
+            if (o == c) break;
+            h = (h + 1) & (T2 - 1);
+        }
+        overflow |= probe == T2;
+    }
+    if (overflow) atomicOr(a.status, kStatusHashOverflow);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+    if (lane == 0) a.counts[unit] = fresh;
+    __syncwarp();
+}
+
 template <int TEAM, int PER>
 __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1) k_sym_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
@@ -201,13 +450,17 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
         const int w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
         team = blockIdx.x * wpb + w;
         nteams = gridDim.x * wpb;
-        sm = smem + w * SymLayout<CAP>::bytes;
+        sm = smem + w * WSymLayout<CAP>::bytes;
     } else {
         team = blockIdx.x;
         nteams = gridDim.x;
         sm = smem;
     }
-    for (int i = begin + team; i < end; i += nteams) sym_row<TEAM, PER>(a, __ldg(a.list + i), sm);
+    if constexpr (TEAM == 32) {
+        for (int i = begin + team; i < end; i += nteams) sym_row_warp<PER>(a, __ldg(a.list + i), sm);
+    } else {
+        for (int i = begin + team; i < end; i += nteams) sym_row<TEAM, PER>(a, __ldg(a.list + i), sm);
+    }
 }
 
 // ------------------------------------------------------------------- numeric
@@ -546,53 +799,10 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     T val[PER];
     int hh[PER];  // slot in bucket (low 16 bits) | instance << 16
     {
-        const int p0 = lane * PER;
-        int t = 0, tb = 0, te = 0, ti = -1, bs = 0;
-        const int* bcol = nullptr;
-        const T* bval = nullptr;
-        T av = T(1);
-        if (p0 < u) {
-            int lo = 0, hi = nA;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (m_pre[mid] <= p0) lo = mid; else hi = mid;
-            }
-            t = lo;
-            tb = m_pre[t];
-            te = m_pre[t + 1];
-            bs = m_bs[t];
-            av = m_a[t];
-            ti = m_inst[t];
-            bcol = a.inst[ib + ti].bcol;
-            bval = reinterpret_cast<const T*>(a.inst[ib + ti].bval);
-        }
+        int ins[PER];
+        gather_chunks<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, lane, col, val, ins);
 #pragma unroll
-        for (int s = 0; s < PER; ++s) {
-            const int p = p0 + s;
-            col[s] = -1;
-            val[s] = T(0);
-            hh[s] = 0;
-            if (p < u) {
-                while (p >= te) {
-                    ++t;
-                    tb = te;
-                    te = m_pre[t + 1];
-                    bs = m_bs[t];
-                    av = m_a[t];
-                    const int tn = m_inst[t];
-                    if (tn != ti) {
-                        ti = tn;
-                        bcol = a.inst[ib + ti].bcol;
-                        bval = reinterpret_cast<const T*>(a.inst[ib + ti].bval);
-                    }
-                }
-                const int f = bs + (p - tb);
-                col[s] = __ldg(bcol + f);
-                const T bv = __ldg(bval + f);
-                val[s] = a.merge ? bv : mul_rn(av, bv);
-                hh[s] = ti << 16;
-            }
-        }
+        for (int e = 0; e < PER; ++e) hh[e] = ins[e] << 16;
     }
     // bucket counts; the second arrival in a bucket lists it for sorting
     int nwl = 0;
@@ -654,7 +864,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
             xcol[pos] = col[s];
             xval[pos] = val[s];
             if (!distinct) {
-                xp[pos] = (unsigned short)(lane * PER + s);
+                xp[pos] = (unsigned short)chunk_product<PER>(lane, s);
                 if (multi) xinst[pos] = (unsigned char)(hh[s] >> 16);
             }
         }

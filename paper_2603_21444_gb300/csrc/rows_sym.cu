@@ -15,7 +15,7 @@ int sym_smem_bytes(int variant, int wpb) {
     int bytes = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        bytes = SymLayout<SS::CAP>::bytes * (SS::TEAM == 32 ? wpb : 1);
+        bytes = SS::TEAM == 32 ? WSymLayout<SS::CAP>::bytes * wpb : SymLayout<SS::CAP>::bytes;
         return cudaSuccess;
     });
     return bytes;
