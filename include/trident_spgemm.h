@@ -68,7 +68,8 @@ typedef enum {
     SPGEMM_ERR_HASH_OVERFLOW = 8,   /* an accumulator saw more entries than sized for */
     SPGEMM_ERR_NOT_CANONICAL = 9,   /* input failed validation */
     SPGEMM_ERR_INTERNAL = 10,       /* device consistency check failed */
-    SPGEMM_ERR_UNSUPPORTED = 11     /* valid request this build does not handle */
+    SPGEMM_ERR_UNSUPPORTED = 11,    /* valid request this build does not handle */
+    SPGEMM_ERR_CAPACITY = 12        /* an output buffer is smaller than the result */
 } spgemm_status;
 
 typedef enum { SPGEMM_F32 = 0, SPGEMM_F64 = 1 } spgemm_dtype;
@@ -160,6 +161,26 @@ spgemm_status spgemm_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const sp
  * A and B patterns.  Rows are written sorted.  Asynchronous (no host sync). */
 spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
                              const spgemm_csr_in* B, spgemm_csr_out* C, spgemm_stream_t stream);
+
+/* spgemm_products: *total (host) = sum over rows of the intermediate-product
+ * count u_i = sum_{k in A_i} |B_k| (2 x total = the product's flop count),
+ * an upper bound of nnz(C).  Synchronises once. */
+spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B, int64_t* total,
+                              spgemm_stream_t stream);
+
+/* spgemm_fused: C = A B in a single pass, without a separate symbolic pass,
+ * into caller buffers of `capacity` entries (C->col_idx, C->val; C->row_ptr
+ * of A.nrows + 1 entries is written; spgemm_products gives a capacity that
+ * always suffices).  When every row fits the warp-team variants, rows are
+ * handed out in order, each row is sorted and reduced on chip, and its output
+ * offset is the sum of the earlier rows' counts (decoupled look-back, with a
+ * bounded wait that reports SPGEMM_ERR_DEVICE_TIMEOUT instead of stalling).
+ * Otherwise the call runs the symbolic and numeric passes.  Values and
+ * pattern are identical to spgemm_symbolic + spgemm_numeric.  *c_nnz (host)
+ * receives nnz(C); SPGEMM_ERR_CAPACITY if it exceeds capacity (outputs then
+ * unspecified).  Synchronises once (twice on the two-pass route). */
+spgemm_status spgemm_fused(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                           spgemm_csr_out* C, int64_t capacity, int64_t* c_nnz, spgemm_stream_t stream);
 
 /* ------------------------------------ ordered sum of partials (Sec. 4.4, Alg. 1)
  *

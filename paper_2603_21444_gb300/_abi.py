@@ -21,7 +21,7 @@ STATUS = {
     0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID_ARG", 2: "SPGEMM_ERR_SHAPE", 3: "SPGEMM_ERR_DTYPE",
     4: "SPGEMM_ERR_INDEX_OVERFLOW", 5: "SPGEMM_ERR_OOM", 6: "SPGEMM_ERR_CUDA", 7: "SPGEMM_ERR_DEVICE_TIMEOUT",
     8: "SPGEMM_ERR_HASH_OVERFLOW", 9: "SPGEMM_ERR_NOT_CANONICAL", 10: "SPGEMM_ERR_INTERNAL",
-    11: "SPGEMM_ERR_UNSUPPORTED",
+    11: "SPGEMM_ERR_UNSUPPORTED", 12: "SPGEMM_ERR_CAPACITY",
 }
 
 
@@ -69,6 +69,9 @@ SIGNATURES = {
     "spgemm_numeric": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P],
                        ctypes.c_int),
     "spgemm_merge": ([P, ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),
+    "spgemm_products": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), I64P, P], ctypes.c_int),
+    "spgemm_fused": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut),
+                      ctypes.c_int64, I64P, P], ctypes.c_int),
     "spgemm_batched": ([P, ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), I32,
                         ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, ctypes.POINTER(Tune), P], ctypes.c_int),
     "spgemm_tile_split": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), I32, ctypes.POINTER(I32), I32,

@@ -175,6 +175,38 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None
     return numeric_into(A, B, C, handle, stream)
 
 
+def products(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None) -> int:
+    """Sum over rows of the intermediate-product counts (an upper bound of nnz(C))."""
+    h = handle or default_handle()
+    tot = ctypes.c_int64()
+    a, b = A.as_in(), B.as_in()
+    check(_abi.lib().spgemm_products(h.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(tot), _stream(stream)),
+          "spgemm_products")
+    return int(tot.value)
+
+
+def fused_into(A: DeviceCSR, B: DeviceCSR, C: DeviceCSR, handle: Handle | None = None, stream=None) -> int:
+    """Single-pass C = A B into C's buffers (capacity = C.col.numel()); returns nnz(C)."""
+    h = handle or default_handle()
+    a, b, c = A.as_in(), B.as_in(), C.as_out()
+    nnz = ctypes.c_int64()
+    check(_abi.lib().spgemm_fused(h.ptr, _dtype_code(A.val.dtype), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                  C.col.numel(), ctypes.byref(nnz), _stream(stream)), "spgemm_fused")
+    return int(nnz.value)
+
+
+def spgemm_single_pass(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """C = A B without a separate symbolic pass (buffers sized by the product count)."""
+    cap = products(A, B, handle, stream)
+    dev = A.row_ptr.device
+    C = DeviceCSR(A.nrows, B.ncols, torch.empty(A.nrows + 1, dtype=torch.int32, device=dev),
+                  torch.empty(cap, dtype=torch.int32, device=dev), torch.empty(cap, dtype=A.val.dtype, device=dev))
+    nnz = fused_into(A, B, C, handle, stream)
+    C.col = C.col[:nnz]
+    C.val = C.val[:nnz]
+    return C
+
+
 # ------------------------------------------------------------------ merge
 
 def merge(parts: list[DeviceCSR], handle: Handle | None = None, stream=None) -> DeviceCSR:

@@ -244,9 +244,13 @@ struct Validate {
 };
 
 // One call of the engine: product (merge == false) or ordered sum of partials.
+// fused_cap >= 0: single-pass product (one group) into that many entries;
+// SPGEMM_ERR_UNSUPPORTED when the rows do not fit the warp-team variants.
+// products_only: analysis only, *c_nnz = sum of the rows' product counts.
 spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<InstDev>& inst,
                   std::vector<GroupDev> groups, bool sizing, int64_t* c_nnz, const spgemm_tune& tune,
-                  const std::vector<Validate>& checks, cudaStream_t st) {
+                  const std::vector<Validate>& checks, cudaStream_t st, long long fused_cap = -1,
+                  bool products_only = false) {
     for (GroupDev& G : groups) G.ncols_inv = (1ull << 63) / (unsigned long long)std::max(G.ncols, 1);
     int dev = -1;
     TSG_CHECK(cudaGetDevice(&dev));
@@ -273,8 +277,12 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             if (groups[g].nrows == 0) TSG_CHECK(cudaMemsetAsync(groups[g].crp, 0, sizeof(int), st));
     }
     if (U == 0) {
-        if (sizing && c_nnz)
+        if ((sizing || products_only) && c_nnz)
             for (int g = 0; g < ngroups; ++g) c_nnz[g] = 0;
+        if (fused_cap >= 0) {
+            for (int g = 0; g < ngroups; ++g) TSG_CHECK(cudaMemsetAsync(groups[g].crp, 0, sizeof(int), st));
+            if (c_nnz) c_nnz[0] = 0;
+        }
         return SPGEMM_OK;
     }
 
@@ -369,7 +377,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         }
     }
 
-    const bool reuse = !sizing && h->plan_valid && h->plan_sig == sig;
+    const bool reuse = !sizing && fused_cap < 0 && !products_only && h->plan_valid && h->plan_sig == sig;
     if (!reuse) {
         h->plan_valid = false;
         PhaseScope ps(h, 0, st);
@@ -386,6 +394,11 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         aa.hist = d_hist;
         aa.counts = d_counts;
         aa.sizing = sizing ? 1 : 0;
+        aa.total_u = nullptr;
+        if (products_only) {
+            aa.total_u = reinterpret_cast<unsigned long long*>(d_nnz);
+            TSG_CHECK(cudaMemsetAsync(d_nnz, 0, 8, st));
+        }
         TSG_CHECK(launch_analysis(aa, st));
         TSG_CHECK(launch_bin_offsets(d_hist, d_off, d_cur, nslots, st));
         TSG_CHECK(launch_bin_fill(d_bin_of, U, d_off, d_cur, d_list, st));
@@ -406,6 +419,57 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     la.status = d_status;
     la.counts = d_counts;
     const int chunk = heavy_chunk_for(max_ncols);
+
+    if (products_only) {
+        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        *c_nnz = p_nnz[0];
+        return SPGEMM_OK;
+    }
+    if (fused_cap >= 0) {
+        // single pass: all rows must sit in warp-team bins of increasing capacity
+        h->plan_valid = false;
+        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        if (ngroups != 1 || p_hist[nb] > 0) return SPGEMM_ERR_UNSUPPORTED;
+        int bmax = -1;
+        for (int b = 0; b < nb; ++b)
+            if (p_hist[b] > 0) bmax = b;
+        if (bmax < 0) bmax = 0;
+        const int v = tune.bin_kernel[bmax];
+        if (variant_team(v) != 32) return SPGEMM_ERR_UNSUPPORTED;
+        for (int b = 0; b < bmax; ++b)
+            if (p_hist[b] > 0 && variant_cap(tune.bin_kernel[b]) > variant_cap(v)) return SPGEMM_ERR_UNSUPPORTED;
+        const int wv = num_wpb(v, dtype, wpb);
+        int* d_ticket = reinterpret_cast<int*>(sb + o_status);
+        TSG_CHECK(cudaMemsetAsync(d_ticket, 0, 16, st));
+        TSG_CHECK(cudaMemsetAsync(d_ex, 0, 8 * U, st));
+        FusedCtl fc;
+        fc.ticket = d_ticket;
+        fc.lb = reinterpret_cast<unsigned long long*>(d_ex);
+        fc.cap = fused_cap;
+        fc.nunits = (int)U;
+        fc.crp = groups[0].crp;
+        const int occ = std::max(1, num_fused_blocks_per_sm(v, dtype, wv));
+        const long long need = (U + wv - 1) / wv;
+        const int blocks = (int)std::min<long long>(need, (long long)h->sms * occ);
+        {
+            PhaseScope ps(h, 3, st);
+            TSG_CHECK(launch_num_fused(v, dtype, la, fc, blocks, wv, st));
+            ++h->launches;
+        }
+        int* p_total = reinterpret_cast<int*>(p_nnz);
+        TSG_CHECK(cudaMemcpyAsync(p_total, groups[0].crp + U, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        const unsigned status = *p_status;
+        if (status) TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
+        if (status & kStatusTimeout) return SPGEMM_ERR_DEVICE_TIMEOUT;
+        if (status & kStatusCapacity) return SPGEMM_ERR_CAPACITY;
+        if (status & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+        if (c_nnz) c_nnz[0] = *p_total;
+        return SPGEMM_OK;
+    }
 
     if (sizing) {
         {
@@ -524,6 +588,7 @@ const char* spgemm_status_str(spgemm_status s) {
         case SPGEMM_ERR_NOT_CANONICAL: return "input is not a valid CSR matrix";
         case SPGEMM_ERR_INTERNAL: return "device consistency check failed";
         case SPGEMM_ERR_UNSUPPORTED: return "unsupported request";
+        case SPGEMM_ERR_CAPACITY: return "output capacity too small";
     }
     return "unknown status";
 }
@@ -617,6 +682,35 @@ spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
     return run(h, dtype, false, inst, groups, false, nullptr, h->tune, checks,
                reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B, int64_t* total,
+                              spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(A, false) || !csr_in_ok(B, false) || !total) return SPGEMM_ERR_INVALID_ARG;
+    if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, nullptr, nullptr, nullptr, 0}};
+    return run(h, 0, false, inst, groups, false, total, h->tune, {}, reinterpret_cast<cudaStream_t>(stream), -1, true);
+}
+
+spgemm_status spgemm_fused(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                           spgemm_csr_out* C, int64_t capacity, int64_t* c_nnz, spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(A, true) || !csr_in_ok(B, true) || !C || !C->row_ptr || !c_nnz || capacity < 0)
+        return SPGEMM_ERR_INVALID_ARG;
+    if (capacity > 0 && (!C->col_idx || !C->val)) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val, 0}};
+    std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
+                                 {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
+    spgemm_status rc = run(h, dtype, false, inst, groups, false, c_nnz, h->tune, checks, st, capacity);
+    if (rc != SPGEMM_ERR_UNSUPPORTED) return rc;
+    // two-pass route
+    TSG_TRY(spgemm_symbolic(h, A, B, C->row_ptr, c_nnz, stream));
+    if (*c_nnz > capacity) return SPGEMM_ERR_CAPACITY;
+    return spgemm_numeric(h, dtype, A, B, C, stream);
 }
 
 spgemm_status spgemm_merge(spgemm_handle* h, spgemm_dtype dtype, int32_t nparts, const spgemm_csr_in* parts,

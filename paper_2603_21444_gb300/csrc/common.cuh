@@ -64,6 +64,17 @@ enum : unsigned {
     kStatusInternal = 1u,      // a row produced a different count than row_ptr says
     kStatusHashOverflow = 2u,  // a probe sequence ran past the table size
     kStatusNotCanonical = 4u,  // validation failed
+    kStatusTimeout = 8u,       // a bounded device wait ran out
+    kStatusCapacity = 16u,     // output capacity exceeded
+};
+
+// single-pass product: ticket counter and look-back state (rows.cuh)
+struct FusedCtl {
+    int* ticket;                 // next row to hand out
+    unsigned long long* lb;      // per row: flag << 62 | value
+    long long cap;               // entries the output can hold
+    int nunits;                  // rows
+    int* crp;                    // output row_ptr (nunits + 1)
 };
 
 // ------------------------------------------------------------------- helpers

@@ -21,6 +21,7 @@ struct AnalysisArgs {
     int* hist;      // nbins + 2 counters
     int* counts;    // per-unit row nnz (empty rows written here when sizing)
     int sizing;
+    unsigned long long* total_u;  // optional: sum of all rows' product counts
 };
 
 // analysis + binning (rows_misc.cu)
@@ -61,6 +62,9 @@ int num_blocks_per_sm(int variant, int dtype, int warps_per_block);
 cudaError_t launch_sym_rows(int variant, const RowLaunchArgs& a, int blocks, int warps_per_block, cudaStream_t s);
 cudaError_t launch_num_rows(int variant, int dtype, const RowLaunchArgs& a, int blocks, int warps_per_block,
                             cudaStream_t s);
+cudaError_t launch_num_fused(int variant, int dtype, const RowLaunchArgs& a, const FusedCtl& fc, int blocks,
+                             int warps_per_block, cudaStream_t s);
+int num_fused_blocks_per_sm(int variant, int dtype, int warps_per_block);
 cudaError_t launch_sym_heavy(const RowLaunchArgs& a, int blocks, int chunk, cudaStream_t s);
 cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& a, void* dense, int blocks, int chunk,
                              cudaStream_t s);

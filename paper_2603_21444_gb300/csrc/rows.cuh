@@ -683,6 +683,51 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
     Team<TEAM>::sync();
 }
 
+// ------------------------------------------------ single-pass output offsets
+//
+// In the single-pass product the rows are handed out in order (row = ticket)
+// and each row's output offset is the sum of the counts of all earlier rows,
+// found by a decoupled look-back: a row first publishes its count (flag 1),
+// walks back over earlier rows adding their published values until it meets
+// an inclusive prefix (flag 2), then publishes its own inclusive prefix.
+// Every earlier row is already running (tickets go only to running warps),
+// so the walk ends; a bounded spin turns a stall into an error instead.
+
+constexpr int kLookbackSpinLimit = 1 << 22;
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of row t's count c over rows 0..t-1 (called by one lane).
+__device__ __forceinline__ long long lookback_offset(const FusedCtl& fc, int t, long long c, unsigned* status) {
+    st_release_u64(fc.lb + t, (1ull << 62) | (unsigned long long)c);
+    long long excl = 0;
+    int j = t - 1, spins = 0;
+    while (j >= 0) {
+        const unsigned long long w = ld_acquire_u64(fc.lb + j);
+        const unsigned flag = (unsigned)(w >> 62);
+        if (flag == 0) {
+            if (++spins > kLookbackSpinLimit) {
+                atomicOr(status, kStatusTimeout);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        excl += (long long)(w & ((1ull << 62) - 1));
+        if (flag == 2) break;
+        --j;
+    }
+    st_release_u64(fc.lb + t, (2ull << 62) | (unsigned long long)(excl + c));
+    return excl;
+}
+
 // ------------------------------------------------- numeric, warp-team variant
 //
 // The same accumulator as num_row, arranged for SIMT efficiency:
@@ -715,8 +760,8 @@ struct WNumLayout {
     static_assert((oval & 7) == 0, "value array alignment");
 };
 
-template <int PER, typename T>
-__device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm) {
+template <int PER, typename T, bool FUSED = false>
+__device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm, const FusedCtl* fc = nullptr) {
     constexpr int CAP = 32 * PER;
     using L = WNumLayout<CAP, T>;
     int* cnt = reinterpret_cast<int*>(sm + L::cnt);
@@ -735,8 +780,10 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     const int g = unit_group(a.unit_base, a.ngroups, unit);
     const GroupDev& G = a.groups[g];
     const int rho = (int)(unit - a.unit_base[g]);
-    const int row_begin = __ldg(G.crp + rho);
-    const int row_len = __ldg(G.crp + rho + 1) - row_begin;
+    // two-pass: the row's slot comes from the symbolic pass; single pass:
+    // from the look-back once the row's count is known
+    long long row_begin = FUSED ? 0 : __ldg(G.crp + rho);
+    int row_len = FUSED ? -1 : __ldg(G.crp + rho + 1) - (int)row_begin;
     const int ncols = G.ncols;
     const unsigned long long ncols_inv = G.ncols_inv;
     const int ib = G.inst_begin, icount = G.inst_count;
@@ -780,7 +827,10 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         }
     }
     if (nA > L::MAXA || u > CAP) {
-        if (lane == 0) atomicOr(a.status, kStatusInternal);
+        if (lane == 0) {
+            atomicOr(a.status, kStatusInternal);
+            if (FUSED) lookback_offset(*fc, unit, 0, a.status);  // successors must not wait
+        }
         __syncwarp();
         return;
     }
@@ -791,7 +841,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     for (int i = 4 * lane; i <= NB; i += 128) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
     // a row whose nnz equals its product count has no repeated column: it
     // only needs sorting (no tie-break, no run compaction)
-    const bool distinct = row_len == u;
+    bool distinct = !FUSED && row_len == u;
     __syncwarp();
 
     // ---- gather: lane owns products [lane*PER, lane*PER + PER)
@@ -870,6 +920,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         }
     __syncwarp();
 
+    bool repeated = false;
     // ---- sort each listed bucket in place: by column, ties by p
     for (int w = lane; w < nwl; w += 32) {
         const int b = xwl[w];
@@ -906,9 +957,36 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
                 xval[j + 1] = v;
                 if (multi) xinst[j + 1] = ins;
             }
+            if (FUSED)
+                for (int i = lo + 1; i < hi; ++i) repeated |= xcol[i] == xcol[i - 1];
         }
     }
     __syncwarp();
+    if (FUSED) {
+        // the row's count: u when no column repeats, else the number of runs
+        distinct = !__any_sync(0xffffffffu, repeated);
+        int cnt_out = u;
+        if (!distinct) {
+            cnt_out = 0;
+            for (int q = lane; q < u; q += 32) cnt_out += q == 0 || xcol[q] != xcol[q - 1];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt_out += __shfl_xor_sync(0xffffffffu, cnt_out, o);
+        }
+        long long off = 0;
+        if (lane == 0) {
+            off = lookback_offset(*fc, unit, cnt_out, a.status);
+            fc->crp[unit] = (int)off;
+            if (unit == fc->nunits - 1) fc->crp[fc->nunits] = (int)(off + cnt_out);
+            if (off + cnt_out > fc->cap) atomicOr(a.status, kStatusCapacity);
+        }
+        off = __shfl_sync(0xffffffffu, off, 0);
+        if (off + cnt_out > fc->cap) {
+            __syncwarp();
+            return;
+        }
+        row_begin = off;
+        row_len = cnt_out;
+    }
 
     T* cval = reinterpret_cast<T*>(G.cval) + row_begin;
     int* ccol = G.ccol + row_begin;
@@ -989,6 +1067,21 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
         for (int i = begin + team; i < end; i += nteams) num_row_warp<PER, T>(a, __ldg(a.list + i), sm);
     } else {
         for (int i = begin + team; i < end; i += nteams) num_row<TEAM, PER, T>(a, __ldg(a.list + i), sm);
+    }
+}
+
+template <int PER, typename T>
+__global__ void __launch_bounds__(PER <= 8 ? 1024 : 512, 1) k_num_fused(RowArgs a, FusedCtl fc) {
+    extern __shared__ __align__(16) char smem[];
+    constexpr int CAP = 32 * PER;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    char* sm = smem + w * WNumLayout<CAP, T>::bytes;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(fc.ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= fc.nunits) break;
+        num_row_warp<PER, T, true>(a, t, sm, &fc);
     }
 }
 

@@ -43,6 +43,7 @@ __global__ void k_analysis(AnalysisArgs a) {
         }
         a.bin_of[unit] = (unsigned char)bin;
         if (bin == nb + 1 && a.sizing) a.counts[unit] = 0;
+        if (a.total_u && u) atomicAdd(a.total_u, (unsigned long long)u);
     }
     const unsigned active = __ballot_sync(0xffffffffu, bin >= 0);
     if (bin >= 0) {

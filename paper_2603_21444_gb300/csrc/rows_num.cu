@@ -53,6 +53,45 @@ cudaError_t launch_num_rows(int variant, int dtype, const RowLaunchArgs& l, int 
                       : launch_num_rows_t<float>(variant, l, blocks, wpb, s);
 }
 
+template <typename T>
+static cudaError_t launch_num_fused_t(int variant, const RowLaunchArgs& l, const FusedCtl& fc, int blocks, int wpb,
+                                      cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    return dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        if constexpr (SS::TEAM != 32) {
+            return cudaErrorInvalidValue;
+        } else {
+            const int smem = WNumLayout<SS::CAP, T>::bytes * wpb;
+            cudaFuncSetAttribute(k_num_fused<SS::PER, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_num_fused<SS::PER, T><<<blocks, 32 * wpb, smem, s>>>(a, fc);
+            return cudaGetLastError();
+        }
+    });
+}
+
+cudaError_t launch_num_fused(int variant, int dtype, const RowLaunchArgs& l, const FusedCtl& fc, int blocks, int wpb,
+                             cudaStream_t s) {
+    return dtype == 1 ? launch_num_fused_t<double>(variant, l, fc, blocks, wpb, s)
+                      : launch_num_fused_t<float>(variant, l, fc, blocks, wpb, s);
+}
+
+template <typename T>
+static int num_fused_blocks_per_sm_t(int variant, int wpb) {
+    int nb = 0;
+    dispatch_variant(variant, [&](auto S) {
+        using SS = decltype(S);
+        if constexpr (SS::TEAM == 32)
+            nb = blocks_per_sm(k_num_fused<SS::PER, T>, 32 * wpb, WNumLayout<SS::CAP, T>::bytes * wpb);
+        return cudaSuccess;
+    });
+    return nb;
+}
+
+int num_fused_blocks_per_sm(int variant, int dtype, int wpb) {
+    return dtype == 1 ? num_fused_blocks_per_sm_t<double>(variant, wpb) : num_fused_blocks_per_sm_t<float>(variant, wpb);
+}
+
 cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& l, void* dense, int blocks, int chunk, cudaStream_t s) {
     const RowArgs a = to_row_args(l);
     const int smem = (chunk / 32) * 4;

@@ -238,3 +238,55 @@ def test_full_size_er_sampled_rows(tsg, handle):
         o0, o1 = ref.rowptr[t], ref.rowptr[t + 1]
         assert np.array_equal(col[s0:s1], ref.col[o0:o1])
         assert np.array_equal(val[s0:s1], ref.val[o0:o1])
+
+
+def _fused(tsg, A, B, handle, dtype=np.float64, cap=None):
+    dA = tsg.DeviceCSR.from_host(A.astype(dtype))
+    dB = tsg.DeviceCSR.from_host(B.astype(dtype))
+    cap = tsg.products(dA, dB, handle) if cap is None else cap
+    C = tsg.DeviceCSR(A.nrows, B.ncols, torch.empty(A.nrows + 1, dtype=torch.int32, device="cuda"),
+                      torch.empty(cap, dtype=torch.int32, device="cuda"),
+                      torch.empty(cap, dtype=torch.from_numpy(np.zeros(0, dtype)).dtype, device="cuda"))
+    nnz = tsg.fused_into(dA, dB, C, handle)
+    torch.cuda.synchronize()
+    rp, col, val = C.to_host()
+    return rp, col[:nnz], val[:nnz]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_single_pass_er(tsg, handle, dtype):
+    A = gen.er(4096, 4096, 8, 0, dtype)
+    assert_matches(_fused(tsg, A, A, handle, dtype), A, A, dtype)
+
+
+@pytest.mark.parametrize("dmax", [12, 30, 90])
+def test_single_pass_ragged_and_repeats(tsg, handle, dmax):
+    # ragged rows spread over several warp bins (and, for dmax = 90, block
+    # bins: the two-pass route); integer values make repeated columns exact
+    A = gen.er_variable(3000, 500, dmax, 41, np.float64, "int", p_empty=0.1)
+    B = gen.er_variable(500, 700, dmax, 42, np.float64, "int", p_empty=0.1)
+    assert_matches(_fused(tsg, A, B, handle), A, B)
+
+
+def test_single_pass_capacity_error(tsg, handle):
+    from paper_2603_21444_gb300._abi import SpgemmError
+    A = gen.er(2000, 2000, 8, 3)
+    ref, _ = oracle.spgemm(A, A)
+    with pytest.raises(SpgemmError) as e:
+        _fused(tsg, A, A, handle, cap=ref.nnz - 1)
+    assert e.value.code == 12
+    # the handle recovers: the next call succeeds
+    assert_matches(_fused(tsg, A, A, handle), A, A)
+
+
+def test_single_pass_full_size_matches_two_pass(tsg, handle):
+    n, d = 1 << 20, 16
+    A = gen.er(n, n, d, 0)
+    B = gen.er(n, n, d, 1)
+    dA, dB = tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B)
+    C2 = tsg.spgemm(dA, dB, handle)
+    C1 = tsg.spgemm_single_pass(dA, dB, handle)
+    torch.cuda.synchronize()
+    assert torch.equal(C1.row_ptr, C2.row_ptr)
+    assert torch.equal(C1.col, C2.col)
+    assert torch.equal(C1.val, C2.val)
