@@ -280,6 +280,10 @@ def run_native(args):
               "numeric_rows_ms": num_ms, "heavy_ms": phase_ms[4] / args.steps,
               "symbolic_frac_of_hbm": round(sym_bytes / (sym_ms * 1e-3) / 1e9 / peak, 4) if sym_ms > 0 else None}
 
+    single = None
+    if rank == 0:
+        single = bench_single_pass(tsg, h, dA, dB, prods, nnz, args.steps, stream)
+
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = e2e_public_api(tsg, A, B, prods, args)
@@ -298,7 +302,7 @@ def run_native(args):
                            f"{nnz * 12 / 1e9:.2f} GB written per step)"},
                 "roofline": roof, "phases": {k: (round(v, 4) if isinstance(v, float) else v)
                                               for k, v in phases.items()},
-                "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+                "single_pass": single, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if args.extras and world == 1:
             extras = {}
             for name, fn in (("trident_grid", bench_trident), ("many_products", bench_many),
@@ -311,6 +315,41 @@ def run_native(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_single_pass(tsg, h, dA, dB, prods, nnz, steps, stream):
+    """The same product through spgemm_fused: one numeric pass whose row
+    offsets come from a decoupled look-back, output buffers preallocated at
+    capacity nnz(C); checked against the two-pass result's size."""
+    import ctypes
+
+    import torch
+    from paper_2603_21444_gb300 import _abi
+    C = tsg.DeviceCSR(dA.nrows, dB.ncols, torch.empty(dA.nrows + 1, dtype=torch.int32, device="cuda"),
+                      torch.empty(nnz, dtype=torch.int32, device="cuda"),
+                      torch.empty(nnz, dtype=torch.float64, device="cuda"))
+    a_in, b_in, c_out = dA.as_in(), dB.as_in(), C.as_out()
+    box = ctypes.c_int64()
+    L = _abi.lib()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def step():
+        _abi.check(L.spgemm_fused(h.ptr, _abi.F64, ctypes.byref(a_in), ctypes.byref(b_in), ctypes.byref(c_out),
+                                  ctypes.c_int64(nnz), ctypes.byref(box), sptr), "spgemm_fused")
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    if box.value != nnz:
+        return {"error": f"nnz {box.value} != {nnz}"}
+    h.read_timing()
+    h.set_timing(True)
+    ms = _time(step, steps, warmup=0)
+    h.set_timing(False)
+    phase_ms, phase_cnt = h.read_timing()
+    return {"value": round(2 * prods / (ms * 1e-3) / 1e9, 2), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "numeric_fused_ms": round(phase_ms[3] / max(phase_cnt[3], 1), 4),
+            "analysis_ms": round(phase_ms[0] / max(steps, 1), 4), "steps": steps}
 
 
 def e2e_public_api(tsg, A, B, prods, args):

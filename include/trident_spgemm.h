@@ -171,10 +171,11 @@ spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const sp
 /* spgemm_fused: C = A B in a single pass, without a separate symbolic pass,
  * into caller buffers of `capacity` entries (C->col_idx, C->val; C->row_ptr
  * of A.nrows + 1 entries is written; spgemm_products gives a capacity that
- * always suffices).  When every row fits the warp-team variants, rows are
- * handed out in order, each row is sorted and reduced on chip, and its output
- * offset is the sum of the earlier rows' counts (decoupled look-back, with a
- * bounded wait that reports SPGEMM_ERR_DEVICE_TIMEOUT instead of stalling).
+ * always suffices).  When every row fits the warp-team variants, tiles of
+ * consecutive rows (one per warp of a block) are handed out in order, each
+ * row is sorted and reduced on chip, and a tile's output offset is the sum of
+ * the earlier tiles' counts (decoupled look-back, with a bounded wait that
+ * reports SPGEMM_ERR_DEVICE_TIMEOUT instead of stalling).
  * Otherwise the call runs the symbolic and numeric passes.  Values and
  * pattern are identical to spgemm_symbolic + spgemm_numeric.  *c_nnz (host)
  * receives nnz(C); SPGEMM_ERR_CAPACITY if it exceeds capacity (outputs then

@@ -305,7 +305,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     size_t o_off = o_hist + align16(4 * (kMaxBins + 2));
     size_t o_cur = o_off + align16(4 * (kMaxBins + 3));
     size_t o_status = o_cur + align16(4 * (kMaxBins + 2));
-    size_t o_bsum = o_status + 16;
+    size_t o_tick = o_status + 16;
+    size_t o_bsum = o_tick + align16(4 * (kMaxBins + 2));
     size_t o_nnz = o_bsum + align16(8 * nblk);
     size_t o_ubase = o_nnz + align16(8 * ngroups);
     size_t o_inst = o_ubase + align16(8 * (ngroups + 1));
@@ -320,6 +321,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     int* d_hist = reinterpret_cast<int*>(sb + o_hist);
     int* d_off = reinterpret_cast<int*>(sb + o_off);
     int* d_cur = reinterpret_cast<int*>(sb + o_cur);
+    int* d_tick = reinterpret_cast<int*>(sb + o_tick);
     TSG_TRY(grow(h->status, 16, st, true));
     unsigned* d_status = static_cast<unsigned*>(h->status.p);
     long long* d_bsum = reinterpret_cast<long long*>(sb + o_bsum);
@@ -418,6 +420,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     la.merge = merge ? 1 : 0;
     la.status = d_status;
     la.counts = d_counts;
+    la.tick = d_tick;
     const int chunk = heavy_chunk_for(max_ncols);
 
     if (products_only) {
@@ -443,7 +446,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         const int wv = num_wpb(v, dtype, wpb);
         int* d_ticket = reinterpret_cast<int*>(sb + o_status);
         TSG_CHECK(cudaMemsetAsync(d_ticket, 0, 16, st));
-        TSG_CHECK(cudaMemsetAsync(d_ex, 0, 8 * U, st));
+        const long long ntiles = (U + wv - 1) / wv;  // look-back entries: one per tile of wv rows
+        TSG_CHECK(cudaMemsetAsync(d_ex, 0, 8 * ntiles, st));
         FusedCtl fc;
         fc.ticket = d_ticket;
         fc.lb = reinterpret_cast<unsigned long long*>(d_ex);
@@ -451,8 +455,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         fc.nunits = (int)U;
         fc.crp = groups[0].crp;
         const int occ = std::max(1, num_fused_blocks_per_sm(v, dtype, wv));
-        const long long need = (U + wv - 1) / wv;
-        const int blocks = (int)std::min<long long>(need, (long long)h->sms * occ);
+        const int blocks = (int)std::min<long long>(ntiles, (long long)h->sms * occ);
         {
             PhaseScope ps(h, 3, st);
             TSG_CHECK(launch_num_fused(v, dtype, la, fc, blocks, wv, st));
@@ -539,6 +542,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     }
     {
         PhaseScope ps(h, 3, st);
+        TSG_CHECK(cudaMemsetAsync(d_tick, 0, 4 * nslots, st));
         for (int b = 0; b < nb; ++b) {
             if (hist[b] == 0) continue;
             const int v = tune.bin_kernel[b];

@@ -70,8 +70,8 @@ enum : unsigned {
 
 // single-pass product: ticket counter and look-back state (rows.cuh)
 struct FusedCtl {
-    int* ticket;                 // next row to hand out
-    unsigned long long* lb;      // per row: flag << 62 | value
+    int* ticket;                 // next tile of rows to hand out
+    unsigned long long* lb;      // per tile: flag << 62 | value
     long long cap;               // entries the output can hold
     int nunits;                  // rows
     int* crp;                    // output row_ptr (nunits + 1)

@@ -52,6 +52,7 @@ struct RowLaunchArgs {
     int merge;
     unsigned* status;
     int* counts;
+    int* tick;  // per-bin row tickets of the numeric warp-team kernels (zeroed before them)
 };
 // warps per block a warp-team variant can take (launch bound and shared memory)
 int warp_variant_max_wpb(int variant, int per_warp_bytes);

@@ -39,6 +39,7 @@ struct RowArgs {
     int merge;                        // nonzero: instances are partials to add
     unsigned* status;
     int* counts;                      // symbolic: per-unit row nnz
+    int* tick;                        // numeric warp teams: per-bin row tickets, zero at launch
 };
 
 __device__ __forceinline__ int search_pre(const int* m_pre, int nA, int p) {
@@ -685,47 +686,112 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
 
 // ------------------------------------------------ single-pass output offsets
 //
-// In the single-pass product the rows are handed out in order (row = ticket)
-// and each row's output offset is the sum of the counts of all earlier rows,
-// found by a decoupled look-back: a row first publishes its count (flag 1),
-// walks back over earlier rows adding their published values until it meets
-// an inclusive prefix (flag 2), then publishes its own inclusive prefix.
-// Every earlier row is already running (tickets go only to running warps),
-// so the walk ends; a bounded spin turns a stall into an error instead.
+// In the single-pass product a block takes tiles of consecutive rows in
+// order (one row per warp) and each tile's output offset is the sum of the
+// counts of all earlier tiles, found by a decoupled look-back: a tile first
+// publishes its count (flag 1), walks back over earlier tiles adding their
+// published values until it meets an inclusive prefix (flag 2), then
+// publishes its own inclusive prefix.  Every earlier tile belongs to a
+// running block (tickets go only to running blocks), so the walk ends; a
+// bounded spin turns a stall into an error instead.  One entry per tile
+// rather than per row keeps the walks short: per-row entries arrive faster
+// than a walk of 32 entries per memory round trip can follow.
 
 constexpr int kLookbackSpinLimit = 1 << 22;
 
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Exclusive prefix of row t's count c over rows 0..t-1 (called by one lane).
+constexpr int kLookbackPer = 4;  // entries read per lane and round: a window of 128 tiles
+
+// Exclusive prefix of tile t's count c over tiles 0..t-1, called by a whole
+// warp.  One round reads the 128 tiles before position j (lane l, slot k
+// reads tile j - 32k - l; independent loads, one memory round trip): the
+// tiles up to and including the nearest inclusive prefix are summed once all
+// of them have published; otherwise the window moves 128 tiles back.
+// Positions before tile 0 read as an inclusive prefix of 0.  Each entry is
+// one 64-bit word carrying its flag with its value, so relaxed loads suffice.
 __device__ __forceinline__ long long lookback_offset(const FusedCtl& fc, int t, long long c, unsigned* status) {
-    st_release_u64(fc.lb + t, (1ull << 62) | (unsigned long long)c);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) st_release_u64(fc.lb + t, (1ull << 62) | (unsigned long long)c);
     long long excl = 0;
     int j = t - 1, spins = 0;
     while (j >= 0) {
-        const unsigned long long w = ld_acquire_u64(fc.lb + j);
-        const unsigned flag = (unsigned)(w >> 62);
-        if (flag == 0) {
+        unsigned long long w[kLookbackPer];
+#pragma unroll
+        for (int k = 0; k < kLookbackPer; ++k) {
+            const int idx = j - 32 * k - lane;
+            w[k] = idx >= 0 ? ld_relaxed_u64(fc.lb + idx) : (2ull << 62);
+        }
+        // need[k]: lanes of slot k up to and including the nearest inclusive prefix
+        unsigned need[kLookbackPer];
+        bool found = false, wait = false;
+#pragma unroll
+        for (int k = 0; k < kLookbackPer; ++k) {
+            const unsigned incl = __ballot_sync(0xffffffffu, (w[k] >> 62) == 2);
+            const unsigned none = __ballot_sync(0xffffffffu, (w[k] >> 62) == 0);
+            need[k] = found ? 0u : (incl ? ((incl & (0u - incl)) << 1) - 1u : 0xffffffffu);
+            found = found || incl != 0;
+            wait = wait || (none & need[k]) != 0;
+        }
+        if (wait) {
             if (++spins > kLookbackSpinLimit) {
-                atomicOr(status, kStatusTimeout);
+                if (lane == 0) atomicOr(status, kStatusTimeout);
                 break;
             }
             __nanosleep(64);
             continue;
         }
-        excl += (long long)(w & ((1ull << 62) - 1));
-        if (flag == 2) break;
-        --j;
+        long long v = 0;
+#pragma unroll
+        for (int k = 0; k < kLookbackPer; ++k)
+            if ((need[k] >> lane) & 1u) v += (long long)(w[k] & ((1ull << 62) - 1));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (found) break;
+        j -= 32 * kLookbackPer;
     }
-    st_release_u64(fc.lb + t, (2ull << 62) | (unsigned long long)(excl + c));
+    if (lane == 0) st_release_u64(fc.lb + t, (2ull << 62) | (unsigned long long)(excl + c));
     return excl;
+}
+
+// A warp's place in the current tile of the single-pass product.
+struct FusedRow {
+    const FusedCtl* fc;
+    long long* sh;  // shared, one slot per warp of the block
+    int tile, w, nw;
+};
+
+// Output offset of warp fr.w's row (count c) within the whole product.  Every
+// warp of the block calls it exactly once per tile (c = 0 for a warp without
+// a row): the counts are scanned in shared memory and warp 0 resolves the
+// tile's offset by look-back.
+__device__ __forceinline__ long long fused_offset(const FusedRow& fr, long long c, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) fr.sh[fr.w] = c;
+    __syncthreads();
+    if (fr.w == 0) {
+        const long long v = lane < fr.nw ? fr.sh[lane] : 0;
+        long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const long long total = __shfl_sync(0xffffffffu, x, 31);
+        const long long base = lookback_offset(*fr.fc, fr.tile, total, status);
+        if (lane < fr.nw) fr.sh[lane] = base + x - v;
+    }
+    __syncthreads();
+    return fr.sh[fr.w];
 }
 
 // ------------------------------------------------- numeric, warp-team variant
@@ -761,7 +827,7 @@ struct WNumLayout {
 };
 
 template <int PER, typename T, bool FUSED = false>
-__device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm, const FusedCtl* fc = nullptr) {
+__device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm, const FusedRow* fr = nullptr) {
     constexpr int CAP = 32 * PER;
     using L = WNumLayout<CAP, T>;
     int* cnt = reinterpret_cast<int*>(sm + L::cnt);
@@ -827,10 +893,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         }
     }
     if (nA > L::MAXA || u > CAP) {
-        if (lane == 0) {
-            atomicOr(a.status, kStatusInternal);
-            if (FUSED) lookback_offset(*fc, unit, 0, a.status);  // successors must not wait
-        }
+        if (lane == 0) atomicOr(a.status, kStatusInternal);
+        if (FUSED) fused_offset(*fr, 0, a.status);  // the block and later tiles must not wait
         __syncwarp();
         return;
     }
@@ -972,14 +1036,13 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt_out += __shfl_xor_sync(0xffffffffu, cnt_out, o);
         }
-        long long off = 0;
+        const long long off = fused_offset(*fr, cnt_out, a.status);
+        const FusedCtl* fc = fr->fc;
         if (lane == 0) {
-            off = lookback_offset(*fc, unit, cnt_out, a.status);
             fc->crp[unit] = (int)off;
             if (unit == fc->nunits - 1) fc->crp[fc->nunits] = (int)(off + cnt_out);
             if (off + cnt_out > fc->cap) atomicOr(a.status, kStatusCapacity);
         }
-        off = __shfl_sync(0xffffffffu, off, 0);
         if (off + cnt_out > fc->cap) {
             __syncwarp();
             return;
@@ -1064,7 +1127,19 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
         sm = smem;
     }
     if constexpr (TEAM == 32) {
-        for (int i = begin + team; i < end; i += nteams) num_row_warp<PER, T>(a, __ldg(a.list + i), sm);
+        // rows are handed out one at a time: the per-row cost varies (gather
+        // latency, collisions, the SM's distance to the L2 slices), and a
+        // static stride leaves the slowest warps to finish the bin alone
+        const int lane = threadIdx.x & 31;
+        (void)team;
+        (void)nteams;
+        for (;;) {
+            int i = 0;
+            if (lane == 0) i = begin + atomicAdd(a.tick + a.bin, 1);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= end) break;
+            num_row_warp<PER, T>(a, __ldg(a.list + i), sm);
+        }
     } else {
         for (int i = begin + team; i < end; i += nteams) num_row<TEAM, PER, T>(a, __ldg(a.list + i), sm);
     }
@@ -1073,15 +1148,23 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
 template <int PER, typename T>
 __global__ void __launch_bounds__(PER <= 8 ? 1024 : 512, 1) k_num_fused(RowArgs a, FusedCtl fc) {
     extern __shared__ __align__(16) char smem[];
+    __shared__ long long sh_off[32];
+    __shared__ int sh_tile;
     constexpr int CAP = 32 * PER;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     char* sm = smem + w * WNumLayout<CAP, T>::bytes;
+    FusedRow fr{&fc, sh_off, 0, w, nw};
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(fc.ticket, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= fc.nunits) break;
-        num_row_warp<PER, T, true>(a, t, sm, &fc);
+        if (threadIdx.x == 0) sh_tile = atomicAdd(fc.ticket, 1);
+        __syncthreads();
+        fr.tile = sh_tile;
+        if ((long long)fr.tile * nw >= fc.nunits) break;  // the same for the whole block
+        const int row = fr.tile * nw + w;
+        if (row < fc.nunits)
+            num_row_warp<PER, T, true>(a, row, sm, &fr);
+        else
+            fused_offset(fr, 0, a.status);
     }
 }
 

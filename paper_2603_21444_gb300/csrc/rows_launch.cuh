@@ -18,6 +18,7 @@ inline RowArgs to_row_args(const RowLaunchArgs& l) {
     a.merge = l.merge;
     a.status = l.status;
     a.counts = l.counts;
+    a.tick = l.tick;
     return a;
 }
 
