@@ -1129,15 +1129,17 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
     if constexpr (TEAM == 32) {
         // rows are handed out one at a time: the per-row cost varies (gather
         // latency, collisions, the SM's distance to the L2 slices), and a
-        // static stride leaves the slowest warps to finish the bin alone
+        // static stride leaves the slowest warps to finish the bin alone.
+        // The next ticket is drawn before the current row starts, so the
+        // atomic's round trip overlaps the row.
         const int lane = threadIdx.x & 31;
         (void)team;
         (void)nteams;
+        int nxt = lane == 0 ? atomicAdd(a.tick + a.bin, 1) : 0;
         for (;;) {
-            int i = 0;
-            if (lane == 0) i = begin + atomicAdd(a.tick + a.bin, 1);
-            i = __shfl_sync(0xffffffffu, i, 0);
+            const int i = begin + __shfl_sync(0xffffffffu, nxt, 0);
             if (i >= end) break;
+            if (lane == 0) nxt = atomicAdd(a.tick + a.bin, 1);
             num_row_warp<PER, T>(a, __ldg(a.list + i), sm);
         }
     } else {
@@ -1155,6 +1157,8 @@ __global__ void __launch_bounds__(PER <= 8 ? 1024 : 512, 1) k_num_fused(RowArgs 
     const int nw = blockDim.x >> 5;
     char* sm = smem + w * WNumLayout<CAP, T>::bytes;
     FusedRow fr{&fc, sh_off, 0, w, nw};
+    // a tile is drawn only when the block can start it: a tile drawn ahead
+    // would delay every later tile's offset by a whole tile of work
     for (;;) {
         if (threadIdx.x == 0) sh_tile = atomicAdd(fc.ticket, 1);
         __syncthreads();

@@ -156,7 +156,7 @@ def test_plan_autotune_keeps_bits(tsg, handle):
     Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
     plan = tsg.Plan(As, Bs)
     t = plan.autotune()
-    assert 1 <= t.num_bins <= 12 and 1 <= t.warps_per_block <= 16
+    assert 1 <= t.num_bins <= 12 and 1 <= t.warps_per_block <= 32
     Cs = plan.execute()
     Cs = plan.execute()
     torch.cuda.synchronize()
