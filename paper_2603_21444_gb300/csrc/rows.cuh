@@ -210,10 +210,18 @@ template <typename T>
 struct Vec2 {};
 template <>
 struct Vec2<double> {
+    // p is 16-byte aligned.  At a 32-byte boundary one 256-bit load takes the
+    // lane's whole sector; two 128-bit loads would request it twice.
     static __device__ __forceinline__ void load4(const double* p, double* out) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-        out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+        if ((reinterpret_cast<uintptr_t>(p) & 31) == 0) {
+            asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+                : "=d"(out[0]), "=d"(out[1]), "=d"(out[2]), "=d"(out[3])
+                : "l"(p));
+        } else {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+            const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+            out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+        }
     }
 };
 template <>
