@@ -35,7 +35,7 @@ UNIT = "GFLOP/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--n-log2", type=int, default=20)
@@ -84,31 +84,49 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling every 50 ms; returns once the first sample arrived
+        (at most 5 s), so that the sampler is live when the timed region opens."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.monotonic()
+            while not self.lines and time.monotonic() - t0 < 5:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        """Open the timed window."""
+        self.t_open = time.monotonic()
 
     def stop(self):
+        """Close the window; summarise the samples taken inside it (or, when
+        the window was shorter than one sampling period, the first sample
+        after it opened)."""
         if self.proc is None:
             return None
+        t_close = time.monotonic()
+        time.sleep(0.06)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
+        t_open = getattr(self, "t_open", 0.0)
+        inside = [ln for ts, ln in self.lines if t_open <= ts <= t_close]
+        if not inside:
+            inside = [ln for ts, ln in self.lines if ts >= t_open][:1]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -122,7 +140,8 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "window_ms": round((t_close - t_open) * 1e3, 1)}
 
 
 def measured_traffic():
@@ -245,6 +264,7 @@ def run_native(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -282,7 +302,7 @@ def run_native(args):
 
     single = None
     if rank == 0:
-        single = bench_single_pass(tsg, h, dA, dB, prods, nnz, args.steps, stream)
+        single = bench_single_pass(tsg, h, dA, dB, prods, nnz, min(args.steps, 20), stream)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -308,7 +328,7 @@ def run_native(args):
             for name, fn in (("trident_grid", bench_trident), ("many_products", bench_many),
                              ("autograd", bench_autograd), ("markov_clustering", bench_mcl)):
                 try:
-                    extras[name] = fn(tsg, max(3, args.steps // 4))
+                    extras[name] = fn(tsg, 3)
                 except Exception as ex:  # report, keep the main line
                     extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
             line["workloads"] = extras
@@ -380,7 +400,7 @@ def e2e_public_api(tsg, A, B, prods, args):
 
     nnz = step()
     torch.cuda.synchronize()
-    steps = max(3, args.steps // 4)
+    steps = min(max(3, args.steps // 4), 10)
     t0 = time.perf_counter()
     for _ in range(steps):
         step()

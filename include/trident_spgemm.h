@@ -102,10 +102,12 @@ typedef struct {
  * products a team holds on chip):
  *   0: warp,  32   1: warp, 64    2: warp, 128    3: warp, 256    4: warp, 512
  *   5: 128 threads, 1024   6: 256 threads, 2048   7: 512 threads, 4096
- *   8: 512 threads, 8192
- * A variant whose capacity is below bin_upper is rejected. */
+ *   8: 512 threads, 8192   9: warp, 384
+ * The default bins are 32, 64, 128, 256, 384, 512, ..., 8192 with variants
+ * 0, 1, 2, 3, 9, 4, 5, 6, 7, 8.  A variant whose capacity is below bin_upper
+ * is rejected. */
 #define SPGEMM_MAX_BINS 12
-#define SPGEMM_NUM_VARIANTS 9
+#define SPGEMM_NUM_VARIANTS 10
 enum { SPGEMM_ACC_SORT = 0 };
 
 typedef struct {
@@ -116,7 +118,8 @@ typedef struct {
     int32_t warps_per_block;               /* blocks of warp-team variants: 1..32 (clamped per
                                               variant to what its shared memory allows) */
     int32_t validate;                      /* nonzero: check inputs on the device */
-    int32_t sym_warps_per_block;           /* symbolic pass; 0 = warps_per_block */
+    int32_t sym_warps_per_block;           /* symbolic pass; 0 = warps_per_block (clamped to 8 for
+                                              warp variants up to 384, 16 above) */
 } spgemm_tune;
 
 typedef struct spgemm_handle spgemm_handle;

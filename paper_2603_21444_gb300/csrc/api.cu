@@ -133,11 +133,12 @@ spgemm_status grow_pinned(spgemm_handle* h, size_t bytes) {
 
 void default_tune(spgemm_tune* t) {
     std::memset(t, 0, sizeof(*t));
-    const int upper[9] = {32, 64, 128, 256, 512, 1024, 2048, 4096, 8192};
-    t->num_bins = 9;
-    for (int b = 0; b < 9; ++b) {
+    const int upper[10] = {32, 64, 128, 256, 384, 512, 1024, 2048, 4096, 8192};
+    const int kernel[10] = {0, 1, 2, 3, 9, 4, 5, 6, 7, 8};
+    t->num_bins = 10;
+    for (int b = 0; b < 10; ++b) {
         t->bin_upper[b] = upper[b];
-        t->bin_kernel[b] = b;
+        t->bin_kernel[b] = kernel[b];
     }
     t->accumulator = SPGEMM_ACC_SORT;
     t->warps_per_block = 16;
@@ -216,8 +217,10 @@ struct PhaseScope {
 
 // warps per block of variant v for the requested setting (clamped to what
 // the variant's launch bound and shared memory allow)
-int sym_wpb(int v, int wpb) { return std::min(wpb, warp_variant_max_wpb(v, sym_smem_bytes(v, 1))); }
-int num_wpb(int v, int dtype, int wpb) { return std::min(wpb, warp_variant_max_wpb(v, num_smem_bytes(v, dtype, 1))); }
+int sym_wpb(int v, int wpb) { return std::min(wpb, warp_variant_max_wpb(v, sym_smem_bytes(v, 1), true)); }
+int num_wpb(int v, int dtype, int wpb) {
+    return std::min(wpb, warp_variant_max_wpb(v, num_smem_bytes(v, dtype, 1), false));
+}
 
 void occupancy(spgemm_handle* h, int wpb, int swpb) {
     if (h->occ_wpb == wpb * 64 + swpb) return;
@@ -1386,7 +1389,7 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
     {
         // one size up: every bin served by the next larger variant
         spgemm_tune t = base;
-        for (int b = 0; b + 1 < t.num_bins; ++b) t.bin_kernel[b] = b + 1;
+        for (int b = 0; b + 1 < t.num_bins; ++b) t.bin_kernel[b] = base.bin_kernel[b + 1];
         cand.push_back(t);
     }
     {

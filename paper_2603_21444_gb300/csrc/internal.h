@@ -55,7 +55,7 @@ struct RowLaunchArgs {
     int* tick;  // per-bin row tickets of the numeric warp-team kernels (zeroed before them)
 };
 // warps per block a warp-team variant can take (launch bound and shared memory)
-int warp_variant_max_wpb(int variant, int per_warp_bytes);
+int warp_variant_max_wpb(int variant, int per_warp_bytes, bool symbolic);
 int sym_smem_bytes(int variant, int warps_per_block);
 int num_smem_bytes(int variant, int dtype, int warps_per_block);
 int sym_blocks_per_sm(int variant, int warps_per_block);

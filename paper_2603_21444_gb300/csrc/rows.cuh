@@ -313,10 +313,92 @@ __device__ __forceinline__ void gather_chunks(const RowArgs& a, int ib, int nA, 
     }
 }
 
+// ------------------------------------------------- strided warp gather
+//
+// For rows of at most 32 A entries whose B rows are short, a chunk of 4
+// would often straddle two B rows or start off a 16-byte boundary and fall
+// back to element loads.  There lane L takes product p = 32 s + L in slot s
+// instead: one warp instruction reads 32 consecutive products, i.e. whole
+// B rows, coalesced whatever their lengths and alignment.  Lane t holds A
+// entry t (first product, B-row pointers, a value, instance) in registers.
+// In each round of 32 products the entries starting inside the round set
+// one bit each of a mask; the owner of product p is the entry with the
+// highest start at or below p, else the owner carried over from the
+// previous round, and its fields come from lane t by shuffles.
+
+constexpr int kStridedMaxAvg = 16;  // strided when the mean B-row length is below this
+
+template <int PER>
+__device__ __forceinline__ bool use_strided(int nA, int u) {
+    return PER >= 4 && nA <= 32 && u < kStridedMaxAvg * nA;
+}
+
+// owner_at: 32 ints of the warp's shared memory, free during the gather.
+template <int PER, bool VALS, typename T>
+__device__ __forceinline__ void gather_strided(const RowArgs& a, int ib, int nA, int u, const int* m_pre,
+                                               const int* m_bs, const T* m_a, const unsigned char* m_inst,
+                                               int* owner_at, int lane, int (&col)[PER], T (&val)[PER],
+                                               int (&ins)[PER]) {
+    constexpr int kNone = 0x7fffffff;  // start of an entry that owns no product
+    int e_start = kNone, e_ins = 0;
+    unsigned long long e_col = 0, e_val = 0;
+    T e_av = T(0);
+    if (lane < nA) {
+        const int s0 = m_pre[lane];
+        if (m_pre[lane + 1] > s0) e_start = s0;
+        e_ins = m_inst[lane];
+        const InstDev& I = a.inst[ib + e_ins];
+        const int bs = m_bs[lane];
+        e_col = reinterpret_cast<unsigned long long>(I.bcol + bs);
+        if (VALS) {
+            e_val = reinterpret_cast<unsigned long long>(reinterpret_cast<const T*>(I.bval) + bs);
+            e_av = m_a[lane];
+        }
+    }
+    int carry = 0;
+#pragma unroll
+    for (int s = 0; s < PER; ++s) {
+        col[s] = -1;
+        if (VALS) val[s] = T(0);
+        ins[s] = 0;
+        const int base = 32 * s;
+        if (base >= u) continue;
+        const int rel = e_start - base;
+        const bool head = rel >= 0 && rel < 32;
+        const unsigned heads = __reduce_or_sync(0xffffffffu, head ? 1u << rel : 0u);
+        if (head) owner_at[rel] = lane;
+        __syncwarp();
+        const unsigned below = heads & (0xffffffffu >> (31 - lane));
+        const int t = below ? owner_at[31 - __clz(below)] : carry;
+        __syncwarp();
+        carry = __shfl_sync(0xffffffffu, t, 31);
+        const int ts = __shfl_sync(0xffffffffu, e_start, t);
+        const unsigned long long cp = __shfl_sync(0xffffffffu, e_col, t);
+        const int ti = __shfl_sync(0xffffffffu, e_ins, t);
+        unsigned long long vp = 0;
+        T av = T(0);
+        if (VALS) {
+            vp = __shfl_sync(0xffffffffu, e_val, t);
+            av = __shfl_sync(0xffffffffu, e_av, t);
+        }
+        const int p = base + lane;
+        if (p < u) {
+            const int off = p - ts;
+            col[s] = __ldg(reinterpret_cast<const int*>(cp) + off);
+            if (VALS) {
+                const T bv = __ldg(reinterpret_cast<const T*>(vp) + off);
+                val[s] = a.merge ? bv : mul_rn(av, bv);
+            }
+            ins[s] = ti;
+        }
+    }
+}
+
 // ------------------------------------------------ symbolic, warp-team variant
 //
 // Same count as sym_row (first insertions into a shared-memory hash set of
-// 4 pow2ceil(u) slots), arranged for SIMT efficiency: every product makes one
+// 4 pow2ceil(u) slots, at most the largest power of two within 4 CAP),
+// arranged for SIMT efficiency: every product makes one
 // insertion attempt at its home slot, all slots of a lane issued together;
 // the products that met a different column there (about one in eight) are
 // compacted into a list and finish their linear probe one per lane.  The
@@ -327,6 +409,7 @@ template <int CAP>
 struct WSymLayout {
     static constexpr int MAXA = CAP / 2;
     static constexpr int TBL = 4 * CAP;
+    static constexpr int TBL2 = pow2floor_c(TBL);                  // largest table used (a power of two)
     static constexpr int table = 0;                                // int[TBL]
     static constexpr int clist = 4 * TBL;                          // int[CAP] collided columns
     static constexpr int bytes = (clist + 4 * CAP + 15) & ~15;
@@ -400,11 +483,15 @@ __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* s
     {
         float unused_val[PER];
         int unused_ins[PER];
-        gather_chunks<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, lane, col, unused_val,
-                                         unused_ins);
+        if (use_strided<PER>(nA, u))
+            gather_strided<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, clist, lane, col,
+                                              unused_val, unused_ins);
+        else
+            gather_chunks<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, lane, col, unused_val,
+                                             unused_ins);
     }
     __syncwarp();  // the meta is dead: the table takes its place
-    const int T2 = 4 * pow2ceil(u);
+    const int T2 = min(4 * pow2ceil(u), L::TBL2);
     const int shift = 32 - (31 - __clz(T2));
     for (int i = 4 * lane; i < T2; i += 128) *reinterpret_cast<int4*>(table + i) = make_int4(-1, -1, -1, -1);
     __syncwarp();
@@ -449,7 +536,8 @@ __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* s
 }
 
 template <int TEAM, int PER>
-__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1) k_sym_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 12 ? 256 : 512) : TEAM,
+                                    TEAM == 32 && PER <= 12 ? (PER == 12 ? 3 : 5) : 1) k_sym_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -817,7 +905,7 @@ __device__ __forceinline__ long long fused_offset(const FusedRow& fr, long long 
 template <int CAP, typename T>
 struct WNumLayout {
     static constexpr int MAXA = CAP / 2;
-    static constexpr int NBMAX = 2 * CAP;
+    static constexpr int NBMAX = 2 * pow2floor_c(CAP);             // most buckets (a power of two)
     static constexpr int cnt = 0;                                  // int[NBMAX + 4]
     static constexpr int ocol = (NBMAX + 4) * 4;                   // int[CAP]
     static constexpr int oval = ocol + 4 * CAP;                    // T[CAP]
@@ -907,7 +995,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         return;
     }
     if (lane == 0) m_pre[nA] = u;
-    const int NB = 2 * pow2ceil(u);
+    const int NB = min(2 * pow2ceil(u), L::NBMAX);
     Bucketer bk;
     bk.init(ncols, ncols_inv, NB);
     for (int i = 4 * lane; i <= NB; i += 128) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
@@ -916,13 +1004,18 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     bool distinct = !FUSED && row_len == u;
     __syncwarp();
 
-    // ---- gather: lane owns products [lane*PER, lane*PER + PER)
+    // ---- gather (chunked or strided product order; xp records p)
     int col[PER];
     T val[PER];
     int hh[PER];  // slot in bucket (low 16 bits) | instance << 16
+    const bool strided = use_strided<PER>(nA, u);
     {
         int ins[PER];
-        gather_chunks<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, lane, col, val, ins);
+        if (strided)
+            gather_strided<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, reinterpret_cast<int*>(wl), lane,
+                                         col, val, ins);
+        else
+            gather_chunks<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, lane, col, val, ins);
 #pragma unroll
         for (int e = 0; e < PER; ++e) hh[e] = ins[e] << 16;
     }
@@ -986,7 +1079,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
             xcol[pos] = col[s];
             xval[pos] = val[s];
             if (!distinct) {
-                xp[pos] = (unsigned short)chunk_product<PER>(lane, s);
+                xp[pos] = (unsigned short)(strided ? 32 * s + lane : chunk_product<PER>(lane, s));
                 if (multi) xinst[pos] = (unsigned char)(hh[s] >> 16);
             }
         }
@@ -1118,7 +1211,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
 }
 
 template <int TEAM, int PER, typename T>
-__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1) k_num_rows(RowArgs a) {
+__global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : (PER == 12 ? 256 : 512)) : TEAM,
+                                    TEAM == 32 && PER == 12 ? 3 : 1) k_num_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -1156,7 +1250,8 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : 512) : TEAM, 1
 }
 
 template <int PER, typename T>
-__global__ void __launch_bounds__(PER <= 8 ? 1024 : 512, 1) k_num_fused(RowArgs a, FusedCtl fc) {
+__global__ void __launch_bounds__(PER <= 8 ? 1024 : (PER == 12 ? 256 : 512), PER == 12 ? 3 : 1)
+    k_num_fused(RowArgs a, FusedCtl fc) {
     extern __shared__ __align__(16) char smem[];
     __shared__ long long sh_off[32];
     __shared__ int sh_tile;

@@ -42,6 +42,7 @@ inline cudaError_t dispatch_variant(int v, F&& f) {
         case 6: return f(VariantShape<6>());
         case 7: return f(VariantShape<7>());
         case 8: return f(VariantShape<8>());
+        case 9: return f(VariantShape<9>());
         default: return cudaErrorInvalidValue;
     }
 }

@@ -4,9 +4,12 @@
 
 namespace tsg {
 
-int warp_variant_max_wpb(int variant, int per_warp_bytes) {
+int warp_variant_max_wpb(int variant, int per_warp_bytes, bool symbolic) {
     if (variant_team(variant) != 32) return 1;
-    const int by_threads = variant_per(variant) <= 8 ? 32 : 16;
+    const int per = variant_per(variant);
+    // the kernels' launch bounds: symbolic 256 threads up to 12 per lane
+    // (registers for 5 resp. 3 blocks per SM), numeric 1024 up to 8
+    const int by_threads = symbolic ? (per <= 12 ? 8 : 16) : (per <= 8 ? 32 : (per == 12 ? 8 : 16));
     const int by_smem = (227 * 1024) / per_warp_bytes;
     return by_smem < by_threads ? by_smem : by_threads;
 }
