@@ -290,3 +290,32 @@ def test_single_pass_full_size_matches_two_pass(tsg, handle):
     assert torch.equal(C1.row_ptr, C2.row_ptr)
     assert torch.equal(C1.col, C2.col)
     assert torch.equal(C1.val, C2.val)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("da,db", [(32, 10), (40, 8), (12, 30), (20, 3), (31, 12), (6, 50)])
+def test_gather_orders_and_384_variant(tsg, handle, dtype, da, db):
+    # the strided gather (at most 32 A entries, mean B row below 16), the
+    # chunked gather (more A entries or long B rows) and the 384-product warp
+    # variant (u in (256, 384]) against the oracle, bit for bit; repeated
+    # columns come from a narrow B
+    A = gen.er(3000, 1500, da, 71 + da, dtype, "normal")
+    B = gen.er(1500, 600, db, 72 + db, dtype, "normal")
+    assert_matches(run_product(tsg, A, B, handle, dtype), A, B, dtype)
+
+
+def test_gather_orders_ragged_b_rows(tsg, handle):
+    # B rows of every length 0..24 at every alignment; A rows of 0..16
+    # entries, so that u <= 384 and every row fits either forced variant
+    A = gen.er_variable(4000, 3000, 16, 81, np.float64, "normal", p_empty=0.05)
+    B = gen.er_variable(3000, 900, 24, 82, np.float64, "normal", p_empty=0.1)
+    assert_matches(run_product(tsg, A, B, handle), A, B)
+    # the same rows forced onto the 384 variant and onto the 512 variant
+    for kernel, upper in ((9, 384), (4, 512)):
+        t = tsg.default_tune()
+        t.num_bins = 1
+        t.bin_upper[0] = upper
+        t.bin_kernel[0] = kernel
+        handle.set_tune(t)
+        assert_matches(run_product(tsg, A, B, handle), A, B)
+    handle.set_tune(None)
