@@ -301,7 +301,7 @@ def run_native(args):
               "symbolic_frac_of_hbm": round(sym_bytes / (sym_ms * 1e-3) / 1e9 / peak, 4) if sym_ms > 0 else None}
 
     single = None
-    if rank == 0:
+    if rank == 0 and args.extras:
         single = bench_single_pass(tsg, h, dA, dB, prods, nnz, min(args.steps, 20), stream)
 
     e2e = None

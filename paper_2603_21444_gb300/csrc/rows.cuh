@@ -1152,13 +1152,15 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         row_len = cnt_out;
     }
 
+    // output rows are stored evict-first: they are not read again here, and
+    // the B rows that later rows gather should keep their place in L2
     T* cval = reinterpret_cast<T*>(G.cval) + row_begin;
     int* ccol = G.ccol + row_begin;
     if (distinct) {
         // ---- sorted products are the row: copy out
         for (int q = lane; q < u; q += 32) {
-            ccol[q] = xcol[q];
-            cval[q] = xval[q];
+            __stcs(ccol + q, xcol[q]);
+            __stcs(cval + q, xval[q]);
         }
         __syncwarp();
         return;
@@ -1199,8 +1201,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
             }
             const int idx = nout + __popc(hm & lt);
             if (idx < row_len) {
-                ccol[idx] = c;
-                cval[idx] = res;
+                __stcs(ccol + idx, c);
+                __stcs(cval + idx, res);
             }
         }
         nout += __popc(hm);
