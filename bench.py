@@ -326,7 +326,8 @@ def run_native(args):
         if args.extras and world == 1:
             extras = {}
             for name, fn in (("trident_grid", bench_trident), ("many_products", bench_many),
-                             ("autograd", bench_autograd), ("markov_clustering", bench_mcl)):
+                             ("autograd", bench_autograd), ("restriction", bench_restriction),
+                             ("permutation", bench_permutation), ("markov_clustering", bench_mcl)):
                 try:
                     extras[name] = fn(tsg, 3)
                 except Exception as ex:  # report, keep the main line
@@ -544,6 +545,72 @@ def bench_autograd(tsg, steps):
             "nnz_c": pat.C.nnz, "forward_ms": round(fwd_ms, 3), "forward_with_sizing_ms": round(fresh_ms, 3),
             "backward_ms": round(bwd_ms, 3), "backward_deterministic_ms": round(det_ms, 3),
             "fwd_plus_bwd_ms": round(fb_ms, 3), "forward_gflops": round(2 * prods / fwd_ms / 1e6, 2)}
+
+
+def bench_restriction(tsg, steps):
+    """C = A R: A the main ER matrix (n = 2^20, 16 per row, float64), R an
+    unsmoothed-aggregation restriction operator (n x n/4, one entry per
+    row); sized and computed every step."""
+    import ctypes
+
+    import torch
+    import gen
+    from paper_2603_21444_gb300 import _abi
+    n = 1 << 20
+    A = gen.er(n, n, 16, 0)
+    R = gen.aggregation(n, 4, 7)
+    prods = products(A, R)
+    dA, dR = tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(R)
+    h = tsg.Handle()
+    C = tsg.spgemm(dA, dR, h)
+    a_in, r_in, c_out = dA.as_in(), dR.as_in(), C.as_out()
+    box = ctypes.c_int64()
+    L = _abi.lib()
+    sptr = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        _abi.check(L.spgemm_symbolic(h.ptr, ctypes.byref(a_in), ctypes.byref(r_in), ctypes.c_void_p(c_out.row_ptr),
+                                     ctypes.byref(box), sptr), "symbolic")
+        _abi.check(L.spgemm_numeric(h.ptr, _abi.F64, ctypes.byref(a_in), ctypes.byref(r_in), ctypes.byref(c_out),
+                                    sptr), "numeric")
+
+    ms = _time(step, max(steps, 10), warmup=3)
+    h.close()
+    return {"workload": "C = A R, A ER n=2^20 d=16 f64, R aggregation n x n/4 (ratio 4, seed 7)",
+            "products": prods, "nnz_c": C.nnz, "ms": round(ms, 4), "gflops": round(2 * prods / ms / 1e6, 2)}
+
+
+def bench_permutation(tsg, steps):
+    """Random relabelling of a banded matrix (Sec. 5, permuted HV15R):
+    the permutation kernel's time, the trident imbalance (max / mean nnz per
+    process at P = 256, lambda = 4) before and after, and the product A A
+    of each on one GPU."""
+    import torch
+    import gen
+    n = 1 << 20
+    X = gen.banded(n, [-(n // 4), 0, n // 4], 4, 8)
+    dX = tsg.DeviceCSR.from_host(X)
+    h = tsg.Handle()
+    rp = torch.from_numpy(gen.random_permutation(n, 9)).cuda()
+    cp = torch.from_numpy(gen.random_permutation(n, 10)).cuda()
+    Y = tsg.permute(dX, rp, cp, h)
+    ms_perm = _time(lambda: tsg.permute(dX, rp, cp, h), max(steps, 5), warmup=1)
+    moved = 2 * (X.nnz * 12 + 4 * (n + 1)) + 8 * n
+    out = {"workload": f"banded n=2^20, bands at 0 and +-n/4, half-width 4 ({X.nnz} nnz), f64; symmetric random "
+                       "relabelling of rows and columns",
+           "permute_ms": round(ms_perm, 4), "permute_gbs": round(moved / ms_perm / 1e6, 1)}
+    for name, M in (("banded", dX), ("permuted", Y)):
+        loads = np.array(tsg.trident_loads(M, 8, 4, h), dtype=np.float64)
+        out[f"imbalance_{name}_P256"] = round(float(loads.max() / loads.mean()), 3)
+        C = tsg.spgemm(M, M, h)
+        ms = _time(lambda: tsg.spgemm(M, M, h), max(steps, 3), warmup=1)
+        out[f"product_{name}_ms"] = round(ms, 3)
+        del C
+    out["products"] = products(X, X)
+    out["product_banded_gflops"] = round(2 * out["products"] / out["product_banded_ms"] / 1e6, 2)
+    out["product_permuted_gflops"] = round(2 * out["products"] / out["product_permuted_ms"] / 1e6, 2)
+    h.close()
+    return out
 
 
 def bench_mcl(tsg, steps):

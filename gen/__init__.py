@@ -224,3 +224,43 @@ def permutation_matrix(perm: np.ndarray, dtype=np.float64) -> CSR:
     """P with P[i, perm[i]] = 1, so (P @ X)[i] = X[perm[i]]."""
     n = perm.size
     return CSR(n, n, np.arange(n + 1, dtype=np.int64), perm.astype(np.int32), np.ones(n, dtype=dtype))
+
+
+def aggregation(n: int, ratio: int, seed: int, dtype=np.float64) -> CSR:
+    """Unsmoothed-aggregation restriction operator R (n x ceil(n / ratio)) of
+    an algebraic-multigrid setup: a seeded permutation assigns node i to
+    aggregate perm[i] // ratio, so every aggregate holds ``ratio`` nodes (the
+    last one the remainder), and R[i, aggregate(i)] = 1: one entry per row.
+    C = A R then adds, per row of A, the entries whose columns share an
+    aggregate."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    ncols = -(-n // ratio)
+    cols = (perm // ratio).astype(np.int32)
+    return CSR(n, ncols, np.arange(n + 1, dtype=np.int64), cols, np.ones(n, dtype=dtype))
+
+
+def banded(n: int, offsets, half_width: int, seed: int, dtype=np.float64, values: str = "uniform") -> CSR:
+    """A structured matrix of diagonal bands: row i holds the columns
+    i + o + w for every offset o in ``offsets`` and w in [-half_width,
+    half_width] that fall inside [0, n), deduplicated (the kind of
+    multi-band pattern whose 2D tiles are very uneven).  Values from a seeded
+    stream."""
+    offs = np.unique(np.asarray(offsets, dtype=np.int64))
+    w = np.arange(-half_width, half_width + 1, dtype=np.int64)
+    rel = np.unique((offs[:, None] + w[None, :]).reshape(-1))
+    rows = np.repeat(np.arange(n, dtype=np.int64), rel.size)
+    cols = (np.arange(n, dtype=np.int64)[:, None] + rel[None, :]).reshape(-1)
+    keep = (cols >= 0) & (cols < n)
+    rows, cols = rows[keep], cols[keep]
+    rng = np.random.default_rng([seed, 0xBA7D])
+    vals = _values(rng, cols.size, dtype, values)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    np.cumsum(rowptr, out=rowptr)
+    return CSR(n, n, rowptr, cols.astype(np.int32), vals)
+
+
+def random_permutation(n: int, seed: int) -> np.ndarray:
+    """A seeded uniform permutation of 0..n-1 (int32)."""
+    return np.random.default_rng([seed, 0x9E37]).permutation(n).astype(np.int32)

@@ -325,6 +325,22 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
 spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
                                    spgemm_csr_out* XT, spgemm_stream_t stream);
 
+/* spgemm_csr_permute: Y = P X Q^T, i.e. Y[row_perm[i], col_perm[j]] =
+ * X[i, j] -- the random relabelling of rows and columns that turns a
+ * structured (banded) matrix into an unstructured one whose trident tiles
+ * carry even shares of the nonzeros (Sec. 5, the permuted HV15R runs).
+ * row_perm (X->nrows int32) and col_perm (X->ncols int32) are device
+ * arrays; NULL means the identity.  Y has X's shape; Y->row_ptr (nrows + 1),
+ * Y->col_idx and Y->val (X->nnz each; val skipped when X->val is NULL) are
+ * caller-allocated.  Y's rows come out sorted (X must have no repeated
+ * column within a row).  Both maps are checked on the device to be
+ * permutations before any entry of Y is written: SPGEMM_ERR_INVALID_ARG
+ * otherwise (Y's row_ptr, col_idx and val then unspecified).  Synchronises
+ * once (the check's result). */
+spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
+                                 const int32_t* row_perm, const int32_t* col_perm, spgemm_csr_out* Y,
+                                 spgemm_stream_t stream);
+
 /* ------------------------------------------- Markov clustering (Sec. 5.6)
  *
  * One iteration of Markov clustering with the expansion step done by this

@@ -24,6 +24,10 @@ Contents (each function names the passage of the paper it follows):
 * ``mcl_step``     one Markov-clustering iteration (Sec. 5.6) on the transposed
                    column-stochastic matrix: expansion, inflation, pruning,
                    top-k selection, renormalisation.
+* ``permute``      Y = P X Q^T by its definition (the random relabelling of
+                   the permuted HV15R runs, Sec. 5).
+* ``trident_loads`` nnz of every process's part of the trident partition
+                   (Sec. 3.2); max / mean is Table 2's imbalance.
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -233,6 +237,34 @@ def trident_partition(A: CSR, B: CSR, q: int, lam: int):
     B_t = [[submatrix(B, kcoarse[r], kcoarse[r + 1], ncoarse[j], ncoarse[j + 1]) for j in range(q)]
            for r in range(q)]
     return A_s, B_t
+
+
+def permute(X: CSR, row_perm=None, col_perm=None) -> CSR:
+    """Y = P X Q^T written out: entry (i, j, v) of X becomes (row_perm[i],
+    col_perm[j], v) of Y (None: the identity); Y's rows sorted by column
+    (Sec. 5, random permutation of rows and columns)."""
+    rows = np.repeat(np.arange(X.nrows, dtype=np.int64), np.diff(X.rowptr))
+    r = rows if row_perm is None else np.asarray(row_perm, dtype=np.int64)[rows]
+    c = X.col.astype(np.int64) if col_perm is None else np.asarray(col_perm, dtype=np.int64)[X.col]
+    order = np.lexsort((c, r))
+    counts = np.bincount(r, minlength=X.nrows)
+    rp = np.zeros(X.nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=rp[1:])
+    return CSR(X.nrows, X.ncols, rp, c[order].astype(np.int32), X.val[order].copy())
+
+
+def trident_loads(X: CSR, q: int, lam: int):
+    """nnz of the part X_{ijk} held by process (i, j, k) when X is cut by the
+    trident partition (Sec. 3.2): q x q coarse tiles, each split into lam row
+    slices.  Returns a (q*lam) x q integer array (row: slice i*lam+k, column:
+    coarse column tile j); max / mean over it is the imbalance of Table 2."""
+    _, fine = trident_bounds(X.nrows, q, lam)
+    coarse, _ = trident_bounds(X.ncols, q, 1)
+    out = np.zeros((q * lam, q), dtype=np.int64)
+    for a in range(q * lam):
+        for b in range(q):
+            out[a, b] = submatrix(X, fine[a], fine[a + 1], coarse[b], coarse[b + 1]).nnz
+    return out
 
 
 def static_cannon_schedule(q: int, i: int, j: int):

@@ -81,6 +81,7 @@ SIGNATURES = {
     "spgemm_backward": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, P,
                          I32, P], ctypes.c_int),
     "spgemm_csr_transpose": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
+    "spgemm_csr_permute": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), P, P, ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_plan_create": ([ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), I32, ctypes.POINTER(I32),
                             ctypes.POINTER(P), I64P, ctypes.POINTER(Tune), P, ctypes.POINTER(P)], ctypes.c_int),
     "spgemm_plan_execute": ([P, ctypes.POINTER(CsrOut), I32, P], ctypes.c_int),

@@ -344,6 +344,53 @@ def tile_split(X: DeviceCSR, row_bounds, col_bounds, handle: Handle | None = Non
     return tiles
 
 
+def permute(X: DeviceCSR, row_perm: torch.Tensor | None = None, col_perm: torch.Tensor | None = None,
+            handle: Handle | None = None, stream=None) -> DeviceCSR:
+    """Y = P X Q^T: Y[row_perm[i], col_perm[j]] = X[i, j] (int32 device maps,
+    None = identity), rows sorted.  Raises if a map is not a permutation."""
+    h = handle or default_handle()
+    dev = X.row_ptr.device
+    for m, n in ((row_perm, X.nrows), (col_perm, X.ncols)):
+        if m is not None and (m.dtype != torch.int32 or m.numel() != n or m.device != dev or not m.is_contiguous()):
+            raise ValueError("maps must be contiguous int32 device tensors of the matching length")
+    Y = DeviceCSR(X.nrows, X.ncols, torch.empty(X.nrows + 1, dtype=torch.int32, device=dev),
+                  torch.empty(X.nnz, dtype=torch.int32, device=dev),
+                  torch.empty(X.nnz, dtype=X.val.dtype, device=dev) if X.val is not None else None)
+    xin, yout = X.as_in(), Y.as_out()
+    dt = X.val.dtype if X.val is not None else torch.float64
+    check(_abi.lib().spgemm_csr_permute(h.ptr, _dtype_code(dt), ctypes.byref(xin),
+                                        ctypes.c_void_p(row_perm.data_ptr() if row_perm is not None else 0),
+                                        ctypes.c_void_p(col_perm.data_ptr() if col_perm is not None else 0),
+                                        ctypes.byref(yout), _stream(stream)), "spgemm_csr_permute")
+    return Y
+
+
+def trident_loads(X: DeviceCSR, q: int, lam: int, handle: Handle | None = None, stream=None):
+    """nnz of every process's part X_{ijk} of the trident partition (q x q
+    coarse tiles, each cut into lam row slices; Sec. 3.2), as q*lam rows of q
+    counts, counted on the device (the sizing pass of the tile split).  Their
+    max / mean is the imbalance of the paper's Table 2."""
+    h = handle or default_handle()
+    _, fine = trident_bounds(X.nrows, q, lam)
+    coarse_c, _ = trident_bounds(X.ncols, q, 1)
+    nrp, ncp = len(fine) - 1, q
+    rb = (ctypes.c_int32 * (nrp + 1))(*fine)
+    cb = (ctypes.c_int32 * (ncp + 1))(*coarse_c)
+    dev = X.row_ptr.device
+    rps = [torch.empty(fine[r + 1] - fine[r] + 1, dtype=torch.int32, device=dev) for r in range(nrp) for _ in range(ncp)]
+    outs = (CsrOut * (nrp * ncp))()
+    for r in range(nrp):
+        for c in range(ncp):
+            outs[r * ncp + c] = CsrOut(fine[r + 1] - fine[r], coarse_c[c + 1] - coarse_c[c], rps[r * ncp + c].data_ptr(),
+                                       None, None)
+    nnz = (ctypes.c_int64 * (nrp * ncp))()
+    xin = X.as_in()
+    dt = X.val.dtype if X.val is not None else torch.float64
+    check(_abi.lib().spgemm_tile_split(h.ptr, _dtype_code(dt), ctypes.byref(xin), nrp, rb, ncp, cb, outs, nnz,
+                                       _stream(stream)), "spgemm_tile_split(size)")
+    return [[int(nnz[r * ncp + c]) for c in range(ncp)] for r in range(nrp)]
+
+
 def trident_schedule(q: int, lam: int):
     """Instances of the static-Cannon rounds (Alg. 1, Eq. 2) from the library:
     (a_tile, b_tile, group_ptr)."""

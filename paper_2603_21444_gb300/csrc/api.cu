@@ -55,6 +55,7 @@ struct spgemm_handle {
     DevBuf tr;      // transpose work and the A^T of the deterministic backward
     DevBuf mcl;     // Markov clustering: bounds, offsets, kept entries
     DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
+    DevBuf perm;    // permutation: target hits, row lengths, scan, long-row list, ranks
     int mcl_n = -1;
     long long mcl_total = 0;
     void* pinned = nullptr;
@@ -645,6 +646,7 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->tr.p) cudaFree(h->tr.p);
     if (h->mcl.p) cudaFree(h->mcl.p);
     if (h->mcl_acc.p) cudaFree(h->mcl_acc.p);
+    if (h->perm.p) cudaFree(h->perm.p);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -946,6 +948,72 @@ spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const s
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     note_stream(h, st);
     return transpose_into(h, dtype, X, XT->row_ptr, XT->col_idx, X->val ? XT->val : nullptr, 0, st);
+}
+
+spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
+                                 const int32_t* row_perm, const int32_t* col_perm, spgemm_csr_out* Y,
+                                 spgemm_stream_t stream) {
+    if (!h || !csr_in_ok(X, false) || !Y || !Y->row_ptr || (X->nnz > 0 && !Y->col_idx))
+        return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (Y->nrows != X->nrows || Y->ncols != X->ncols) return SPGEMM_ERR_SHAPE;
+    if (X->val && X->nnz > 0 && !Y->val) return SPGEMM_ERR_INVALID_ARG;
+    int dev = -1;
+    TSG_CHECK(cudaGetDevice(&dev));
+    if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    note_stream(h, st);
+    const long long nr = X->nrows, nc = X->ncols, nnz = X->nnz;
+    // zeroed part first: hits of both maps and the long-row count
+    const size_t o_hr = 0;
+    const size_t o_hc = o_hr + align16(4 * std::max<long long>(nr, 1));
+    const size_t o_cnt = o_hc + align16(4 * std::max<long long>(nc, 1));
+    const size_t zero_bytes = o_cnt + 16;
+    const size_t o_len = zero_bytes;
+    const size_t o_bsum = o_len + align16(4 * std::max<long long>(nr, 1));
+    const size_t o_ex = o_bsum + align16(8 * scan_blocks(std::max<long long>(nr, 1)));
+    const size_t o_list = o_ex + align16(8 * (nr + 1));
+    const size_t o_rank = o_list + align16(4 * std::max<long long>(nr, 1));
+    const size_t bytes = o_rank + align16(4 * std::max<long long>(nnz, 1));
+    TSG_TRY(grow(h->perm, bytes));
+    TSG_TRY(grow(h->status, 16, st, true));
+    char* b = static_cast<char*>(h->perm.p);
+    unsigned* d_status = static_cast<unsigned*>(h->status.p);
+    PhaseScope ps(h, 6, st);
+    TSG_CHECK(cudaMemsetAsync(b, 0, zero_bytes, st));
+    PermuteArgs p{};
+    p.dtype = dtype == SPGEMM_F64 ? 1 : 0;
+    p.nrows = (int)nr;
+    p.ncols = (int)nc;
+    p.nnz = nnz;
+    p.rp = X->row_ptr;
+    p.col = X->col_idx;
+    p.val = X->val;
+    p.row_perm = row_perm;
+    p.col_perm = col_perm;
+    p.yrp = Y->row_ptr;
+    p.ycol = Y->col_idx;
+    p.yval = X->val ? Y->val : nullptr;
+    p.hits_r = reinterpret_cast<int*>(b + o_hr);
+    p.hits_c = reinterpret_cast<int*>(b + o_hc);
+    p.long_count = reinterpret_cast<int*>(b + o_cnt);
+    p.ylen = reinterpret_cast<int*>(b + o_len);
+    p.bsum = reinterpret_cast<long long*>(b + o_bsum);
+    p.ex = reinterpret_cast<long long*>(b + o_ex);
+    p.long_list = reinterpret_cast<int*>(b + o_list);
+    p.rank = reinterpret_cast<int*>(b + o_rank);
+    p.status = d_status;
+    p.sms = h->sms;
+    TSG_CHECK(launch_permute(p, st));
+    h->launches += (row_perm ? 2 : 0) + (col_perm ? 2 : 0) + 1 + 4 + 2;
+    unsigned status = 0;
+    TSG_CHECK(cudaStreamSynchronize(st));
+    TSG_CHECK(cudaMemcpy(&status, d_status, 4, cudaMemcpyDeviceToHost));
+    if (status & kStatusBadMap) {
+        TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    return SPGEMM_OK;
 }
 
 spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,

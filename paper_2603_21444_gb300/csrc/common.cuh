@@ -69,6 +69,7 @@ enum : unsigned {
     kStatusNotCanonical = 4u,  // validation failed
     kStatusTimeout = 8u,       // a bounded device wait ran out
     kStatusCapacity = 16u,     // output capacity exceeded
+    kStatusBadMap = 32u,       // a row or column map is not a permutation
 };
 
 // single-pass product: ticket counter and look-back state (rows.cuh)

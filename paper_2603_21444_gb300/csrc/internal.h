@@ -133,4 +133,30 @@ cudaError_t launch_split_count(const int* rp, const int* col, int nrows, const i
 cudaError_t launch_split_fill(int dtype, const int* rp, const int* col, const void* val, int nrows, const int* rb,
                               int nrp, const int* cb, int ncp, const GroupDev* tiles, cudaStream_t s);
 
+// ---- permutation Y = P X Q^T (permute.cu)
+struct PermuteArgs {
+    int dtype;  // 0 float, 1 double
+    int nrows, ncols;
+    long long nnz;
+    const int* rp;
+    const int* col;
+    const void* val;       // may be null (pattern only)
+    const int* row_perm;   // null: identity
+    const int* col_perm;   // null: identity
+    int* yrp;
+    int* ycol;
+    void* yval;
+    int* hits_r;           // nrows, zeroed
+    int* hits_c;           // ncols, zeroed
+    int* ylen;             // nrows
+    long long* bsum;       // scan_blocks(nrows)
+    long long* ex;         // nrows + 1
+    int* long_count;       // 1, zeroed
+    int* long_list;        // nrows
+    int* rank;             // nnz
+    unsigned* status;
+    int sms;
+};
+cudaError_t launch_permute(const PermuteArgs& p, cudaStream_t s);
+
 }  // namespace tsg
