@@ -292,7 +292,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
 
     // ---- workspace
     if (U > h->units_cap) {
-        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1));
+        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1)) + align16(4 * U);
         TSG_TRY(grow(h->units, bytes));
         h->units_cap = U;
         h->plan_valid = false;
@@ -303,6 +303,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     int* d_counts = reinterpret_cast<int*>(ub + align16(h->units_cap) + align16(4 * h->units_cap));
     long long* d_ex =
         reinterpret_cast<long long*>(ub + align16(h->units_cap) + 2 * align16(4 * h->units_cap));
+    int* d_glist = reinterpret_cast<int*>(ub + align16(h->units_cap) + 2 * align16(4 * h->units_cap) +
+                                          align16(8 * (h->units_cap + 1)));
 
     const long long nblk = scan_blocks(U);
     size_t o_hist = 0;
@@ -310,7 +312,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     size_t o_cur = o_off + align16(4 * (kMaxBins + 3));
     size_t o_status = o_cur + align16(4 * (kMaxBins + 2));
     size_t o_tick = o_status + 16;
-    size_t o_bsum = o_tick + align16(4 * (kMaxBins + 2));
+    size_t o_bsum = o_tick + align16(4 * (kMaxBins + 3));  // per-bin tickets, then the deferred-row count
     size_t o_nnz = o_bsum + align16(8 * nblk);
     size_t o_ubase = o_nnz + align16(8 * ngroups);
     size_t o_inst = o_ubase + align16(8 * (ngroups + 1));
@@ -425,6 +427,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     la.status = d_status;
     la.counts = d_counts;
     la.tick = d_tick;
+    la.glist = nullptr;  // deferral only in the numeric pass of the two-pass product
+    la.gcount = d_tick + nslots;
     const int chunk = heavy_chunk_for(max_ncols);
 
     if (products_only) {
@@ -546,7 +550,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     }
     {
         PhaseScope ps(h, 3, st);
-        TSG_CHECK(cudaMemsetAsync(d_tick, 0, 4 * nslots, st));
+        TSG_CHECK(cudaMemsetAsync(d_tick, 0, 4 * (nslots + 1), st));
+        la.glist = d_glist;
         for (int b = 0; b < nb; ++b) {
             if (hist[b] == 0) continue;
             const int v = tune.bin_kernel[b];
@@ -558,6 +563,10 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wv, st));
             ++h->launches;
         }
+        // rows the bins deferred (clustered columns, many repeats)
+        TSG_CHECK(launch_num_grouped(dtype, la, h->sms, st));
+        ++h->launches;
+        la.glist = nullptr;
     }
     if (tune.validate) {
         TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));

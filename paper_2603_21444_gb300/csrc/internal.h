@@ -53,6 +53,8 @@ struct RowLaunchArgs {
     unsigned* status;
     int* counts;
     int* tick;  // per-bin row tickets of the numeric warp-team kernels (zeroed before them)
+    int* glist;   // rows the numeric kernels defer to the grouped kernel (null: no deferral)
+    int* gcount;  // their count (zeroed before the numeric kernels)
 };
 // warps per block a warp-team variant can take (launch bound and shared memory)
 int warp_variant_max_wpb(int variant, int per_warp_bytes, bool symbolic);
@@ -63,6 +65,8 @@ int num_blocks_per_sm(int variant, int dtype, int warps_per_block);
 cudaError_t launch_sym_rows(int variant, const RowLaunchArgs& a, int blocks, int warps_per_block, cudaStream_t s);
 cudaError_t launch_num_rows(int variant, int dtype, const RowLaunchArgs& a, int blocks, int warps_per_block,
                             cudaStream_t s);
+// rows the numeric kernels deferred (a.glist, *a.gcount), one warp each
+cudaError_t launch_num_grouped(int dtype, const RowLaunchArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_num_fused(int variant, int dtype, const RowLaunchArgs& a, const FusedCtl& fc, int blocks,
                              int warps_per_block, cudaStream_t s);
 int num_fused_blocks_per_sm(int variant, int dtype, int warps_per_block);

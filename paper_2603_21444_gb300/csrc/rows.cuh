@@ -40,6 +40,8 @@ struct RowArgs {
     unsigned* status;
     int* counts;                      // symbolic: per-unit row nnz
     int* tick;                        // numeric warp teams: per-bin row tickets, zero at launch
+    int* glist;                       // numeric: rows deferred to the grouped kernel (null: none)
+    int* gcount;                      // their count, zero at launch
 };
 
 __device__ __forceinline__ int search_pre(const int* m_pre, int nA, int p) {
@@ -562,6 +564,241 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 12 ? 256 : 512) : TEAM,
 
 // ------------------------------------------------------------------- numeric
 
+// ---------------------------------------------- grouped accumulation
+//
+// Rows whose products repeat their columns many times over (banded or
+// stencil-like inputs: u products onto nnz(C_i) <= u / 4 columns that sit
+// next to each other) defeat the bucket sort: a monotone bucket map puts a
+// whole cluster of columns into one bucket, and sorting inside crowded
+// buckets costs their size squared.  The numeric kernels defer such rows
+// (known from the symbolic pass: u >= kGroupedDup nnz(C_i), with few
+// columns and A entries) to k_num_grouped: one warp per row keeps one
+// accumulator per distinct column in a shared-memory hash table and feeds
+// it the products strictly in p order -- 32 at a time, the lanes of one
+// column added by their lowest lane in lane (= p) order -- so every entry
+// is summed in the same order as the bucket path (each instance's products,
+// then the instance sums in order) and the result is identical bit for
+// bit.  Only the distinct columns are sorted at the end (bitonic network).
+
+constexpr int kGroupedDup = 4;      // deferred when u >= 4 nnz(C_i)
+constexpr int kGroupedMaxD = 128;   // at most this many output columns
+constexpr int kGroupedMaxA = 128;   // at most this many A entries (over the row's instances)
+constexpr int kGroupedSlots = 2 * kGroupedMaxD;
+constexpr int kGroupedWarps = 8;
+
+__device__ __forceinline__ bool grouped_row(const RowArgs& a, int nA, int u, int row_len) {
+    return a.glist != nullptr && row_len > 0 && row_len <= kGroupedMaxD && nA <= kGroupedMaxA &&
+           u >= kGroupedDup * row_len;
+}
+
+template <typename T>
+struct GroupedLayout {
+    static constexpr int m_pre = 0;                                     // int[MAXA + 1]
+    static constexpr int m_bs = m_pre + 4 * (kGroupedMaxA + 1);         // int[MAXA]
+    static constexpr int m_a = (m_bs + 4 * kGroupedMaxA + 7) & ~7;      // T[MAXA]
+    static constexpr int m_inst = m_a + (int)sizeof(T) * kGroupedMaxA;  // u8[MAXA]
+    static constexpr int keys = 0;                                      // u64[MAXD], aliases the meta
+    static constexpr int key = (m_inst + kGroupedMaxA + 15) & ~15;      // int[SLOTS] column per slot
+    static constexpr int acc = key + 4 * kGroupedSlots;                 // T[SLOTS] sum of finished instances
+    static constexpr int sub = acc + (int)sizeof(T) * kGroupedSlots;    // T[SLOTS] running sum of one instance
+    static constexpr int st = sub + (int)sizeof(T) * kGroupedSlots;     // int[SLOTS] instance | 256 if acc set
+    static constexpr int stage_v = st + 4 * kGroupedSlots;              // T[32] this round's values
+    static constexpr int stage_i = stage_v + (int)sizeof(T) * 32;       // int[32] this round's instances
+    static constexpr int bytes = (stage_i + 4 * 32 + 15) & ~15;
+    static_assert(8 * kGroupedMaxD <= key, "sorted keys must fit the meta region");
+    static_assert((acc & 7) == 0 && (stage_v & 7) == 0, "value arrays alignment");
+};
+
+template <typename T>
+__device__ __forceinline__ void grouped_row_warp(const RowArgs& a, int unit, char* sm) {
+    using L = GroupedLayout<T>;
+    int* m_pre = reinterpret_cast<int*>(sm + L::m_pre);
+    int* m_bs = reinterpret_cast<int*>(sm + L::m_bs);
+    T* m_a = reinterpret_cast<T*>(sm + L::m_a);
+    unsigned char* m_inst = reinterpret_cast<unsigned char*>(sm + L::m_inst);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(sm + L::keys);
+    int* skey = reinterpret_cast<int*>(sm + L::key);
+    T* sacc = reinterpret_cast<T*>(sm + L::acc);
+    T* ssub = reinterpret_cast<T*>(sm + L::sub);
+    int* sst = reinterpret_cast<int*>(sm + L::st);
+    T* stage_v = reinterpret_cast<T*>(sm + L::stage_v);
+    int* stage_i = reinterpret_cast<int*>(sm + L::stage_i);
+
+    const int lane = threadIdx.x & 31;
+    const int g = unit_group(a.unit_base, a.ngroups, unit);
+    const GroupDev& G = a.groups[g];
+    const int rho = (int)(unit - a.unit_base[g]);
+    const int row_begin = __ldg(G.crp + rho);
+    const int row_len = __ldg(G.crp + rho + 1) - row_begin;
+    const int ib = G.inst_begin, icount = G.inst_count;
+
+    // meta: first product, B-row offset, a_ik, instance per A entry
+    int nA = 0, u = 0;
+    for (int t = 0; t < icount; ++t) {
+        const InstDev& I = a.inst[ib + t];
+        int a0 = 0, a1 = 1;
+        if (!a.merge) {
+            a0 = __ldg(I.arp + rho);
+            a1 = __ldg(I.arp + rho + 1);
+        }
+        for (int e0 = a0; e0 < a1; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < a1;
+            int len = 0, bs = 0;
+            T av = T(1);
+            if (valid) {
+                const int k = a.merge ? rho : __ldg(I.acol + e);
+                bs = __ldg(I.brp + k);
+                len = __ldg(I.brp + k + 1) - bs;
+                if (!a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
+            }
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int idx = nA + lane;
+            if (valid && idx < kGroupedMaxA) {
+                m_pre[idx] = u + x - len;
+                m_bs[idx] = bs;
+                m_a[idx] = av;
+                m_inst[idx] = (unsigned char)t;
+            }
+            nA += min(32, a1 - e0);
+            u += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    if (nA > kGroupedMaxA || row_len > kGroupedMaxD || row_len <= 0) {
+        if (lane == 0) atomicOr(a.status, kStatusInternal);
+        __syncwarp();
+        return;
+    }
+    if (lane == 0) m_pre[nA] = u;
+    const int T2 = 2 * pow2ceil(row_len);  // <= kGroupedSlots
+    const int shift = 32 - (31 - __clz(T2));
+    for (int i = lane; i < T2; i += 32) {
+        skey[i] = -1;
+        sst[i] = -1;
+    }
+    __syncwarp();
+
+    // products in p order, 32 per round (lane L: p = 32 s + L)
+    bool overflow = false;
+    int t = 0;
+    for (int p0 = 0; p0 < u; p0 += 32) {
+        const int p = p0 + lane;
+        int slot = -1;
+        if (p < u) {
+            while (m_pre[t + 1] <= p) ++t;
+            const int ti = m_inst[t];
+            const InstDev& I = a.inst[ib + ti];
+            const int f = m_bs[t] + (p - m_pre[t]);
+            const int c = __ldg(I.bcol + f);
+            const T bv = __ldg(reinterpret_cast<const T*>(I.bval) + f);
+            stage_v[lane] = a.merge ? bv : mul_rn(m_a[t], bv);
+            stage_i[lane] = ti;
+            unsigned h = ((unsigned)c * 0x9E3779B1u) >> shift;
+            for (int probe = 0; probe < T2; ++probe) {
+                const int old = atomicCAS(&skey[h], -1, c);
+                if (old == -1 || old == c) {
+                    slot = (int)h;
+                    break;
+                }
+                h = (h + 1) & (unsigned)(T2 - 1);
+            }
+            overflow |= slot < 0;
+        }
+        __syncwarp();
+        // lanes of one column: the lowest adds them all, in lane order
+        const unsigned peers = __match_any_sync(0xffffffffu, slot >= 0 ? slot : -1 - lane);
+        if (slot >= 0 && (peers & lanemask_lt()) == 0) {
+            int cur = sst[slot];
+            T acc = sacc[slot], sub = ssub[slot];
+            for (unsigned m = peers; m; m &= m - 1) {
+                const int l = __ffs(m) - 1;
+                const T v = stage_v[l];
+                const int ins = stage_i[l];
+                if (cur < 0) {
+                    sub = v;
+                    cur = ins;
+                } else if ((cur & 255) != ins) {
+                    acc = (cur & 256) ? add_rn(acc, sub) : sub;
+                    sub = v;
+                    cur = ins | 256;
+                } else {
+                    sub = add_rn(sub, v);
+                }
+            }
+            sst[slot] = cur;
+            sacc[slot] = acc;
+            ssub[slot] = sub;
+        }
+        __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, overflow)) {
+        if (lane == 0) atomicOr(a.status, kStatusHashOverflow);
+        __syncwarp();
+        return;
+    }
+
+    // the distinct columns, sorted (the meta is dead: keys take its place)
+    int D = 0;
+    for (int i0 = 0; i0 < T2; i0 += 32) {
+        const int i = i0 + lane;
+        const int c = i < T2 ? skey[i] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, c >= 0);
+        if (c >= 0 && D + __popc(m & lanemask_lt()) < kGroupedMaxD)
+            keys[D + __popc(m & lanemask_lt())] = ((unsigned long long)(unsigned)c << 32) | (unsigned)i;
+        D += __popc(m);
+    }
+    if (D != row_len) {
+        if (lane == 0) atomicOr(a.status, kStatusInternal);
+        __syncwarp();
+        return;
+    }
+    int Dp = 32;
+    while (Dp < D) Dp <<= 1;
+    for (int i = D + lane; i < Dp; i += 32) keys[i] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= Dp; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = lane; x < Dp; x += 32) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const unsigned long long kx = keys[x], ky = keys[y];
+                    if ((kx > ky) == ((x & k) == 0)) {
+                        keys[x] = ky;
+                        keys[y] = kx;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    T* cval = reinterpret_cast<T*>(G.cval) + row_begin;
+    int* ccol = G.ccol + row_begin;
+    for (int d = lane; d < D; d += 32) {
+        const unsigned long long kv = keys[d];
+        const int sl = (int)(kv & 0xffffffffu);
+        const int cur = sst[sl];
+        const T res = (cur & 256) ? add_rn(sacc[sl], ssub[sl]) : ssub[sl];
+        __stcs(ccol + d, (int)(kv >> 32));
+        __stcs(cval + d, res);
+    }
+    __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGroupedWarps) k_num_grouped(RowArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int w = threadIdx.x >> 5;
+    char* sm = smem + w * GroupedLayout<T>::bytes;
+    const int n = *a.gcount;
+    for (int i = blockIdx.x * kGroupedWarps + w; i < n; i += gridDim.x * kGroupedWarps)
+        grouped_row_warp<T>(a, __ldg(a.glist + i), sm);
+}
+
 template <int CAP, typename T>
 struct NumLayout {
     static constexpr int MAXA = CAP / 2;
@@ -608,6 +845,11 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
     int nA, u;
     if (!build_meta<TEAM, true, T>(a, G, rho, L::MAXA, CAP, m_bc, m_bv, m_a, m_pre, m_inst, scratch, nA, u)) {
         if (r == 0) atomicOr(a.status, kStatusInternal);
+        return;
+    }
+    if (grouped_row(a, nA, u, row_len)) {
+        if (r == 0) a.glist[atomicAdd(a.gcount, 1)] = unit;
+        Team<TEAM>::sync();
         return;
     }
     // NB = 2 pow2ceil(u) buckets: most products sit alone in their bucket
@@ -991,6 +1233,11 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     if (nA > L::MAXA || u > CAP) {
         if (lane == 0) atomicOr(a.status, kStatusInternal);
         if (FUSED) fused_offset(*fr, 0, a.status);  // the block and later tiles must not wait
+        __syncwarp();
+        return;
+    }
+    if (!FUSED && grouped_row(a, nA, u, row_len)) {
+        if (lane == 0) a.glist[atomicAdd(a.gcount, 1)] = unit;
         __syncwarp();
         return;
     }

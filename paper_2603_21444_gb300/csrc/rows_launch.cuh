@@ -19,6 +19,8 @@ inline RowArgs to_row_args(const RowLaunchArgs& l) {
     a.status = l.status;
     a.counts = l.counts;
     a.tick = l.tick;
+    a.glist = l.glist;
+    a.gcount = l.gcount;
     return a;
 }
 

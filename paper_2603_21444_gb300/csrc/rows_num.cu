@@ -92,6 +92,20 @@ int num_fused_blocks_per_sm(int variant, int dtype, int wpb) {
     return dtype == 1 ? num_fused_blocks_per_sm_t<double>(variant, wpb) : num_fused_blocks_per_sm_t<float>(variant, wpb);
 }
 
+cudaError_t launch_num_grouped(int dtype, const RowLaunchArgs& l, int sms, cudaStream_t s) {
+    const RowArgs a = to_row_args(l);
+    auto go = [&](auto tag) {
+        using T = decltype(tag);
+        const int smem = GroupedLayout<T>::bytes * kGroupedWarps;
+        cudaFuncSetAttribute(k_num_grouped<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int nb = blocks_per_sm(k_num_grouped<T>, 32 * kGroupedWarps, smem);
+        if (nb < 1) nb = 1;
+        k_num_grouped<T><<<sms * nb, 32 * kGroupedWarps, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    return dtype == 1 ? go(double()) : go(float());
+}
+
 cudaError_t launch_num_heavy(int dtype, const RowLaunchArgs& l, void* dense, int blocks, int chunk, cudaStream_t s) {
     const RowArgs a = to_row_args(l);
     const int smem = (chunk / 32) * 4;

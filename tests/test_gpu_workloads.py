@@ -147,3 +147,36 @@ def test_restriction_full_size_sampled_rows(tsg, handle):
     for t, r in enumerate(rows):
         assert np.array_equal(col[rp[r]:rp[r + 1]], ref.col[ref.rowptr[t]:ref.rowptr[t + 1]])
         assert np.array_equal(val[rp[r]:rp[r + 1]], ref.val[ref.rowptr[t]:ref.rowptr[t + 1]])
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("offsets,hw", [([0], 4), ([-700, 0, 700], 4), ([0, 5], 2), ([-1100, 0, 900], 7)])
+def test_banded_products(tsg, handle, dtype, offsets, hw):
+    # clustered, heavily repeated columns: rows deferred to the grouped
+    # accumulation (u >= 4 nnz(C_i), few columns) and rows that stay on the
+    # buckets, all bit-identical to the oracle
+    A = gen.banded(3000, offsets, hw, 11, dtype, "normal")
+    B = gen.banded(3000, offsets, hw, 12, dtype, "normal")
+    C = tsg.spgemm(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), handle)
+    torch.cuda.synchronize()
+    ref, _ = oracle.spgemm(A, B, "f32" if dtype == np.float32 else "f64")
+    _same(C, ref)
+
+
+def test_banded_trident_grid(tsg, handle):
+    # the grouped accumulation with several instances per output row (the
+    # fused trident grid) and with partials (merge mode of the unfused path)
+    n, q, lam = 2048, 4, 2
+    A = gen.banded(n, [-300, 0, 300], 4, 13, np.float64, "normal")
+    B = gen.banded(n, [-300, 0, 300], 4, 14, np.float64, "normal")
+    ref, _ = oracle.trident_product(A, B, q, lam)
+    plan = tsg.TridentPlan(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), q, lam, handle)
+    fused = plan.run_fused(use_graph=False)
+    unfused = plan.run_unfused()
+    torch.cuda.synchronize()
+    for i in range(q):
+        for j in range(q):
+            for k in range(lam):
+                g = plan.block_index(i, j, k)
+                _same(fused[g], ref[i][j][k])
+                _same(unfused[g], ref[i][j][k])
