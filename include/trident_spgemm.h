@@ -102,12 +102,12 @@ typedef struct {
  * products a team holds on chip):
  *   0: warp,  32   1: warp, 64    2: warp, 128    3: warp, 256    4: warp, 512
  *   5: 128 threads, 1024   6: 256 threads, 2048   7: 512 threads, 4096
- *   8: 512 threads, 8192   9: warp, 384
- * The default bins are 32, 64, 128, 256, 384, 512, ..., 8192 with variants
- * 0, 1, 2, 3, 9, 4, 5, 6, 7, 8.  A variant whose capacity is below bin_upper
- * is rejected. */
+ *   8: 512 threads, 8192   9: warp, 384   10: one thread per row, 16
+ * The default bins are 16, 32, 64, 128, 256, 384, 512, ..., 8192 with
+ * variants 10, 0, 1, 2, 3, 9, 4, 5, 6, 7, 8.  A variant whose capacity is
+ * below bin_upper is rejected. */
 #define SPGEMM_MAX_BINS 12
-#define SPGEMM_NUM_VARIANTS 10
+#define SPGEMM_NUM_VARIANTS 11
 enum { SPGEMM_ACC_SORT = 0 };
 
 typedef struct {

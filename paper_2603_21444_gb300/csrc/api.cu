@@ -134,10 +134,10 @@ spgemm_status grow_pinned(spgemm_handle* h, size_t bytes) {
 
 void default_tune(spgemm_tune* t) {
     std::memset(t, 0, sizeof(*t));
-    const int upper[10] = {32, 64, 128, 256, 384, 512, 1024, 2048, 4096, 8192};
-    const int kernel[10] = {0, 1, 2, 3, 9, 4, 5, 6, 7, 8};
-    t->num_bins = 10;
-    for (int b = 0; b < 10; ++b) {
+    const int upper[11] = {16, 32, 64, 128, 256, 384, 512, 1024, 2048, 4096, 8192};
+    const int kernel[11] = {10, 0, 1, 2, 3, 9, 4, 5, 6, 7, 8};
+    t->num_bins = 11;
+    for (int b = 0; b < 11; ++b) {
         t->bin_upper[b] = upper[b];
         t->bin_kernel[b] = kernel[b];
     }
@@ -166,7 +166,9 @@ BinTable bins_of(const spgemm_tune& t) {
     bt.nbins = t.num_bins;
     for (int b = 0; b < t.num_bins; ++b) {
         bt.upper[b] = t.bin_upper[b];
-        bt.amax[b] = variant_cap(t.bin_kernel[b]) / 2;
+        // warp and block teams keep one meta entry per A entry (capacity / 2);
+        // a thread walks its A row directly
+        bt.amax[b] = variant_team(t.bin_kernel[b]) == 1 ? (1 << 30) : variant_cap(t.bin_kernel[b]) / 2;
     }
     return bt;
 }
@@ -233,7 +235,9 @@ void occupancy(spgemm_handle* h, int wpb, int swpb) {
     h->occ_wpb = wpb * 64 + swpb;
 }
 
-int teams_per_block(int v, int wpb) { return variant_team(v) == 32 ? wpb : 1; }
+int teams_per_block(int v, int wpb) {
+    return variant_team(v) == 32 ? wpb : (variant_team(v) == 1 ? kThreadRows : 1);
+}
 
 void note_stream(spgemm_handle* h, cudaStream_t s) {
     h->last_stream = s;

@@ -39,14 +39,16 @@ struct GroupDev {
 };
 
 // kernel variants: team size and capacity (products per team); variant 9,
-// a warp holding 384, sits between 3 and 4 (appended to keep indices stable)
-constexpr int kNumVariants = 10;
+// a warp holding 384, sits between 3 and 4, and variant 10, one thread per
+// row holding 16, below 0 (appended to keep indices stable)
+constexpr int kNumVariants = 11;
 __host__ __device__ constexpr int variant_team(int v) {
-    return (v <= 4 || v == 9) ? 32 : (v == 5 ? 128 : (v == 6 ? 256 : 512));
+    return v == 10 ? 1 : ((v <= 4 || v == 9) ? 32 : (v == 5 ? 128 : (v == 6 ? 256 : 512)));
 }
 __host__ __device__ constexpr int variant_per(int v) {
-    return v <= 4 ? (1 << v) : (v == 9 ? 12 : (v == 8 ? 16 : 8));
+    return v == 10 ? 16 : (v <= 4 ? (1 << v) : (v == 9 ? 12 : (v == 8 ? 16 : 8)));
 }
+constexpr int kThreadRows = 256;  // rows (threads) per block of the thread-per-row variant
 // largest power of two <= x (x >= 1)
 __host__ __device__ constexpr int pow2floor_c(int x) { return x <= 1 ? 1 : 2 * pow2floor_c(x / 2); }
 __host__ __device__ constexpr int variant_cap(int v) { return variant_team(v) * variant_per(v); }

@@ -564,6 +564,174 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 12 ? 256 : 512) : TEAM,
 
 // ------------------------------------------------------------------- numeric
 
+// ------------------------------------------------ thread-per-row variant
+//
+// Rows of at most 16 products (short A rows over short B rows: a
+// restriction operator, ER with a handful of entries per row) leave most of
+// a warp idle.  Here one thread takes a whole row: its products, in p order,
+// go to its own column of a shared array (entry i of thread t at
+// i * kThreadRows + t, so a warp's accesses never share a bank), an
+// insertion sort by column that moves only strictly larger columns keeps
+// equal columns in p order, and each run is summed in that order (each
+// instance's products, then the instance sums in order): the same values
+// as every other variant, bit for bit.
+
+constexpr int kThreadCap = 16;
+
+// The row's products in p order into slots i * kThreadRows (col always,
+// value and instance with VALS); returns u, or -1 past kThreadCap.  A
+// entries are taken 8 at a time with independent loads in three rounds
+// (A entries, B-row bounds, every B row's first entry), so a row waits for
+// a few memory round trips instead of three per A entry.
+constexpr int kThreadBatch = 8;
+
+template <bool VALS, typename T>
+__device__ __forceinline__ int thread_gather(const RowArgs& a, const GroupDev& G, int rho, int* sc, T* sv,
+                                             unsigned char* si) {
+    int n = 0;
+    for (int q = 0; q < G.inst_count; ++q) {
+        const InstDev& I = a.inst[G.inst_begin + q];
+        const T* aval = reinterpret_cast<const T*>(I.aval);
+        const T* bval = reinterpret_cast<const T*>(I.bval);
+        int a0 = 0, a1 = 1;
+        if (!a.merge) {
+            a0 = __ldg(I.arp + rho);
+            a1 = __ldg(I.arp + rho + 1);
+        }
+        for (int e0 = a0; e0 < a1; e0 += kThreadBatch) {
+            int kk[kThreadBatch], b0[kThreadBatch], len[kThreadBatch], c0[kThreadBatch];
+            T av[kThreadBatch], v0[kThreadBatch];
+#pragma unroll
+            for (int e = 0; e < kThreadBatch; ++e) {
+                kk[e] = 0;
+                av[e] = T(1);
+                if (e0 + e < a1) {
+                    kk[e] = a.merge ? rho : __ldg(I.acol + e0 + e);
+                    if (VALS && !a.merge) av[e] = __ldg(aval + e0 + e);
+                }
+            }
+            int tot = 0;
+#pragma unroll
+            for (int e = 0; e < kThreadBatch; ++e) {
+                b0[e] = 0;
+                len[e] = 0;
+                if (e0 + e < a1) {
+                    b0[e] = __ldg(I.brp + kk[e]);
+                    len[e] = __ldg(I.brp + kk[e] + 1) - b0[e];
+                }
+                tot += len[e];
+            }
+            if (n + tot > kThreadCap) return -1;
+#pragma unroll
+            for (int e = 0; e < kThreadBatch; ++e) {
+                c0[e] = 0;
+                v0[e] = T(0);
+                if (len[e] > 0) {
+                    c0[e] = __ldg(I.bcol + b0[e]);
+                    if (VALS) v0[e] = __ldg(bval + b0[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < kThreadBatch; ++e) {
+                if (len[e] == 0) continue;
+                sc[n * kThreadRows] = c0[e];
+                if (VALS) {
+                    sv[n * kThreadRows] = a.merge ? v0[e] : mul_rn(av[e], v0[e]);
+                    si[n * kThreadRows] = (unsigned char)q;
+                }
+                ++n;
+                for (int j = 1; j < len[e]; ++j, ++n) {
+                    sc[n * kThreadRows] = __ldg(I.bcol + b0[e] + j);
+                    if (VALS) {
+                        const T bv = __ldg(bval + b0[e] + j);
+                        sv[n * kThreadRows] = a.merge ? bv : mul_rn(av[e], bv);
+                        si[n * kThreadRows] = (unsigned char)q;
+                    }
+                }
+            }
+        }
+    }
+    return n;
+}
+
+// symbolic counts of thread-per-row rows (defined in rows_sym.cu)
+__global__ void __launch_bounds__(kThreadRows) k_sym_thread(RowArgs a);
+
+template <typename T>
+struct ThreadNumLayout {
+    static constexpr int cols = 0;                                          // int[CAP * ROWS]
+    static constexpr int vals = 4 * kThreadCap * kThreadRows;               // T[CAP * ROWS]
+    static constexpr int inst = vals + (int)sizeof(T) * kThreadCap * kThreadRows;  // u8[CAP * ROWS]
+    static constexpr int bytes = inst + kThreadCap * kThreadRows;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadRows) k_num_thread(RowArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    using L = ThreadNumLayout<T>;
+    int* sc = reinterpret_cast<int*>(smem + L::cols) + threadIdx.x;
+    T* sv = reinterpret_cast<T*>(smem + L::vals) + threadIdx.x;
+    unsigned char* si = reinterpret_cast<unsigned char*>(smem + L::inst) + threadIdx.x;
+    const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
+    for (int i = begin + blockIdx.x * kThreadRows + threadIdx.x; i < end; i += gridDim.x * kThreadRows) {
+        const int unit = __ldg(a.list + i);
+        const int g = unit_group(a.unit_base, a.ngroups, unit);
+        const GroupDev& G = a.groups[g];
+        const int rho = (int)(unit - a.unit_base[g]);
+        const int row_begin = __ldg(G.crp + rho);
+        const int row_len = __ldg(G.crp + rho + 1) - row_begin;
+        const int n = thread_gather<true, T>(a, G, rho, sc, sv, si);
+        if (n < 0) {
+            atomicOr(a.status, kStatusInternal);
+            continue;
+        }
+        for (int x = 1; x < n; ++x) {
+            const int c = sc[x * kThreadRows];
+            const T v = sv[x * kThreadRows];
+            const unsigned char q = si[x * kThreadRows];
+            int y = x - 1;
+            while (y >= 0 && sc[y * kThreadRows] > c) {
+                sc[(y + 1) * kThreadRows] = sc[y * kThreadRows];
+                sv[(y + 1) * kThreadRows] = sv[y * kThreadRows];
+                si[(y + 1) * kThreadRows] = si[y * kThreadRows];
+                --y;
+            }
+            sc[(y + 1) * kThreadRows] = c;
+            sv[(y + 1) * kThreadRows] = v;
+            si[(y + 1) * kThreadRows] = q;
+        }
+        const bool multi = a.merge || G.inst_count > 1;
+        int out = 0;
+        int x = 0;
+        while (x < n) {
+            const int c = sc[x * kThreadRows];
+            T sub = sv[x * kThreadRows], acc = T(0);
+            bool have = false;
+            int ci = si[x * kThreadRows];
+            int y = x + 1;
+            for (; y < n && sc[y * kThreadRows] == c; ++y) {
+                const T v = sv[y * kThreadRows];
+                const int iy = si[y * kThreadRows];
+                if (multi && iy != ci) {
+                    acc = have ? add_rn(acc, sub) : sub;
+                    have = true;
+                    sub = v;
+                    ci = iy;
+                } else {
+                    sub = add_rn(sub, v);
+                }
+            }
+            if (out < row_len) {
+                __stcs(G.ccol + row_begin + out, c);
+                __stcs(reinterpret_cast<T*>(G.cval) + row_begin + out, have ? add_rn(acc, sub) : sub);
+            }
+            ++out;
+            x = y;
+        }
+        if (out != row_len) atomicOr(a.status, kStatusInternal);
+    }
+}
+
 // ---------------------------------------------- grouped accumulation
 //
 // Rows whose products repeat their columns many times over (banded or

@@ -45,6 +45,7 @@ inline cudaError_t dispatch_variant(int v, F&& f) {
         case 7: return f(VariantShape<7>());
         case 8: return f(VariantShape<8>());
         case 9: return f(VariantShape<9>());
+        case 10: return f(VariantShape<10>());
         default: return cudaErrorInvalidValue;
     }
 }

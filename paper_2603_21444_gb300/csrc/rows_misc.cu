@@ -24,6 +24,8 @@ __global__ void k_analysis(AnalysisArgs a) {
             } else {
                 const int a0 = __ldg(I.arp + rho), a1 = __ldg(I.arp + rho + 1);
                 nA += a1 - a0;
+                // unrolled so that the loads of several A entries are in flight at once
+#pragma unroll 8
                 for (int e = a0; e < a1; ++e) {
                     const int k = __ldg(I.acol + e);
                     u += __ldg(I.brp + k + 1) - __ldg(I.brp + k);

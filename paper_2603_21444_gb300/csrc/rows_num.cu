@@ -9,7 +9,10 @@ static int num_smem_bytes_t(int variant, int wpb) {
     int bytes = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        bytes = SS::TEAM == 32 ? WNumLayout<SS::CAP, T>::bytes * wpb : NumLayout<SS::CAP, T>::bytes;
+        if constexpr (SS::TEAM == 1)
+            bytes = ThreadNumLayout<T>::bytes;
+        else
+            bytes = SS::TEAM == 32 ? WNumLayout<SS::CAP, T>::bytes * wpb : NumLayout<SS::CAP, T>::bytes;
         return cudaSuccess;
     });
     return bytes;
@@ -24,8 +27,12 @@ static int num_blocks_per_sm_t(int variant, int wpb) {
     int nb = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
-        nb = blocks_per_sm(k_num_rows<SS::TEAM, SS::PER, T>, threads, num_smem_bytes_t<T>(variant, wpb));
+        if constexpr (SS::TEAM == 1) {
+            nb = blocks_per_sm(k_num_thread<T>, kThreadRows, ThreadNumLayout<T>::bytes);
+        } else {
+            const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+            nb = blocks_per_sm(k_num_rows<SS::TEAM, SS::PER, T>, threads, num_smem_bytes_t<T>(variant, wpb));
+        }
         return cudaSuccess;
     });
     return nb;
@@ -40,10 +47,16 @@ static cudaError_t launch_num_rows_t(int variant, const RowLaunchArgs& l, int bl
     const RowArgs a = to_row_args(l);
     return dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
-        const int smem = num_smem_bytes_t<T>(variant, wpb);
-        cudaFuncSetAttribute(k_num_rows<SS::TEAM, SS::PER, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_num_rows<SS::TEAM, SS::PER, T><<<blocks, threads, smem, s>>>(a);
+        if constexpr (SS::TEAM == 1) {
+            const int smem = ThreadNumLayout<T>::bytes;
+            cudaFuncSetAttribute(k_num_thread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_num_thread<T><<<blocks, kThreadRows, smem, s>>>(a);
+        } else {
+            const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+            const int smem = num_smem_bytes_t<T>(variant, wpb);
+            cudaFuncSetAttribute(k_num_rows<SS::TEAM, SS::PER, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_num_rows<SS::TEAM, SS::PER, T><<<blocks, threads, smem, s>>>(a);
+        }
         return cudaGetLastError();
     });
 }

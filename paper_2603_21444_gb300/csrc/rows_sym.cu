@@ -18,7 +18,10 @@ int sym_smem_bytes(int variant, int wpb) {
     int bytes = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        bytes = SS::TEAM == 32 ? WSymLayout<SS::CAP>::bytes * wpb : SymLayout<SS::CAP>::bytes;
+        if constexpr (SS::TEAM == 1)
+            bytes = 0;  // static shared memory
+        else
+            bytes = SS::TEAM == 32 ? WSymLayout<SS::CAP>::bytes * wpb : SymLayout<SS::CAP>::bytes;
         return cudaSuccess;
     });
     return bytes;
@@ -28,8 +31,12 @@ int sym_blocks_per_sm(int variant, int wpb) {
     int nb = 0;
     dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
-        nb = blocks_per_sm(k_sym_rows<SS::TEAM, SS::PER>, threads, sym_smem_bytes(variant, wpb));
+        if constexpr (SS::TEAM == 1) {
+            nb = blocks_per_sm(k_sym_thread, kThreadRows, 0);
+        } else {
+            const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+            nb = blocks_per_sm(k_sym_rows<SS::TEAM, SS::PER>, threads, sym_smem_bytes(variant, wpb));
+        }
         return cudaSuccess;
     });
     return nb;
@@ -39,12 +46,48 @@ cudaError_t launch_sym_rows(int variant, const RowLaunchArgs& l, int blocks, int
     const RowArgs a = to_row_args(l);
     return dispatch_variant(variant, [&](auto S) {
         using SS = decltype(S);
-        const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
-        const int smem = sym_smem_bytes(variant, wpb);
-        cudaFuncSetAttribute(k_sym_rows<SS::TEAM, SS::PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_sym_rows<SS::TEAM, SS::PER><<<blocks, threads, smem, s>>>(a);
+        if constexpr (SS::TEAM == 1) {
+            k_sym_thread<<<blocks, kThreadRows, 0, s>>>(a);
+        } else {
+            const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
+            const int smem = sym_smem_bytes(variant, wpb);
+            cudaFuncSetAttribute(k_sym_rows<SS::TEAM, SS::PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_sym_rows<SS::TEAM, SS::PER><<<blocks, threads, smem, s>>>(a);
+        }
         return cudaGetLastError();
     });
+}
+
+// Thread-per-row rows: sorted columns in the thread's column of a shared
+// array, distinct ones counted.
+__global__ void __launch_bounds__(kThreadRows) k_sym_thread(RowArgs a) {
+    __shared__ int cols[kThreadCap * kThreadRows];
+    int* sc = cols + threadIdx.x;
+    const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
+    for (int i = begin + blockIdx.x * kThreadRows + threadIdx.x; i < end; i += gridDim.x * kThreadRows) {
+        const int unit = __ldg(a.list + i);
+        const int g = unit_group(a.unit_base, a.ngroups, unit);
+        const GroupDev& G = a.groups[g];
+        const int rho = (int)(unit - a.unit_base[g]);
+        const int n = thread_gather<false, float>(a, G, rho, sc, nullptr, nullptr);
+        if (n < 0) {
+            atomicOr(a.status, kStatusInternal);
+            a.counts[unit] = 0;
+            continue;
+        }
+        for (int x = 1; x < n; ++x) {
+            const int c = sc[x * kThreadRows];
+            int y = x - 1;
+            while (y >= 0 && sc[y * kThreadRows] > c) {
+                sc[(y + 1) * kThreadRows] = sc[y * kThreadRows];
+                --y;
+            }
+            sc[(y + 1) * kThreadRows] = c;
+        }
+        int distinct = 0;
+        for (int x = 0; x < n; ++x) distinct += x == 0 || sc[x * kThreadRows] != sc[(x - 1) * kThreadRows];
+        a.counts[unit] = distinct;
+    }
 }
 
 // Heavy rows: one block per row, a bitmap of `chunk` columns per pass.

@@ -180,3 +180,35 @@ def test_banded_trident_grid(tsg, handle):
                 g = plan.block_index(i, j, k)
                 _same(fused[g], ref[i][j][k])
                 _same(unfused[g], ref[i][j][k])
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_tiny_rows_thread_variant(tsg, handle, dtype):
+    # rows of at most 16 products run one thread per row; ragged rows mix
+    # the thread variant with the warp variants
+    for A, B in ((gen.er(5000, 5000, 4, 41, dtype, "normal"), gen.er(5000, 5000, 4, 42, dtype, "normal")),
+                 (gen.er_variable(4000, 300, 5, 43, dtype, "normal", p_empty=0.1),
+                  gen.er_variable(300, 200, 5, 44, dtype, "normal", p_empty=0.1)),
+                 (gen.er_variable(3000, 2000, 4, 45, dtype, "int"), gen.er(2000, 40, 4, 46, dtype, "int"))):
+        C = tsg.spgemm(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), handle)
+        torch.cuda.synchronize()
+        ref, _ = oracle.spgemm(A, B, "f32" if dtype == np.float32 else "f64")
+        _same(C, ref)
+
+
+def test_tiny_rows_trident_grid(tsg, handle):
+    # several instances (fused) and partials (unfused merge) on tiny rows
+    n, q, lam = 2048, 4, 2
+    A = gen.er(n, n, 4, 47, np.float64, "normal")
+    B = gen.er(n, n, 4, 48, np.float64, "normal")
+    ref, _ = oracle.trident_product(A, B, q, lam)
+    plan = tsg.TridentPlan(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), q, lam, handle)
+    fused = plan.run_fused(use_graph=False)
+    unfused = plan.run_unfused()
+    torch.cuda.synchronize()
+    for i in range(q):
+        for j in range(q):
+            for k in range(lam):
+                g = plan.block_index(i, j, k)
+                _same(fused[g], ref[i][j][k])
+                _same(unfused[g], ref[i][j][k])
