@@ -599,9 +599,16 @@ def bench_permutation(tsg, steps):
     out = {"workload": f"banded n=2^20, bands at 0 and +-n/4, half-width 4 ({X.nnz} nnz), f64; symmetric random "
                        "relabelling of rows and columns",
            "permute_ms": round(ms_perm, 4), "permute_gbs": round(moved / ms_perm / 1e6, 1)}
+    from paper_2603_21444_gb300 import volume
     for name, M in (("banded", dX), ("permuted", Y)):
-        loads = np.array(tsg.trident_loads(M, 8, 4, h), dtype=np.float64)
+        lo = tsg.trident_loads(M, 8, 4, h)
+        loads = np.array(lo, dtype=np.float64)
         out[f"imbalance_{name}_P256"] = round(float(loads.max() / loads.mean()), 3)
+        # Alg. 1 volumes per emulated process at P = 256 (A = B = M), against Prop. 1
+        s = volume.summarize(volume.trident_volumes(lo, lo, 8, 4), 8, 4)
+        model = volume.prop1_volumes(X.nnz, 256, 4)
+        out[f"gi_max_over_prop1_{name}"] = round(s["gi"]["max"] / model["total_gi"], 3)
+        out[f"li_max_over_prop1_{name}"] = round(s["li"]["max"] / model["total_li"], 3)
         C = tsg.spgemm(M, M, h)
         ms = _time(lambda: tsg.spgemm(M, M, h), max(steps, 3), warmup=1)
         out[f"product_{name}_ms"] = round(ms, 3)
