@@ -41,6 +41,14 @@ constexpr int kNumPhases = SPGEMM_NUM_PHASES;
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// The handle's per-unit workspace for `cap` units: bin id (1 B) | list
+// entry (4 B) | count (4 B) | 64-bit exclusive sum (8 B, cap + 1) |
+// deferred-row list (4 B).  Every user sizes it with this one function, so
+// the offsets derived from units_cap stay inside the allocation.
+size_t units_bytes(long long cap) {
+    return align16(cap) + align16(4 * cap) + align16(4 * cap) + align16(8 * (cap + 1)) + align16(4 * cap);
+}
+
 }  // namespace
 
 struct spgemm_handle {
@@ -296,8 +304,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
 
     // ---- workspace
     if (U > h->units_cap) {
-        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1)) + align16(4 * U);
-        TSG_TRY(grow(h->units, bytes));
+        TSG_TRY(grow(h->units, units_bytes(U)));
         h->units_cap = U;
         h->plan_valid = false;
     }
@@ -850,8 +857,7 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
         return SPGEMM_OK;
     }
     if (U > h->units_cap) {
-        const size_t bytes = align16(U) + align16(4 * U) + align16(4 * U) + align16(8 * (U + 1));
-        TSG_TRY(grow(h->units, bytes));
+        TSG_TRY(grow(h->units, units_bytes(U)));
         h->units_cap = U;
     }
     char* ub = static_cast<char*>(h->units.p);

@@ -212,3 +212,17 @@ def test_tiny_rows_trident_grid(tsg, handle):
                 g = plan.block_index(i, j, k)
                 _same(fused[g], ref[i][j][k])
                 _same(unfused[g], ref[i][j][k])
+
+
+def test_split_then_deferred_product_same_handle(tsg, handle):
+    # the tile split sizes the handle's per-unit workspace for rows x column
+    # tiles units; a later product on the same handle, with rows deferred to
+    # the grouped kernel, keeps its deferred-row list inside that workspace
+    X = gen.banded(6000, [-1500, 0, 1500], 4, 3, np.float64, "normal")
+    dX = tsg.DeviceCSR.from_host(X)
+    loads = tsg.trident_loads(dX, 8, 4, handle)
+    assert sum(map(sum, loads)) == X.nnz
+    C = tsg.spgemm(dX, dX, handle)
+    torch.cuda.synchronize()
+    ref, _ = oracle.spgemm(X, X)
+    _same(C, ref)
