@@ -65,6 +65,7 @@ struct spgemm_handle {
     DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
     DevBuf perm;    // permutation: target hits, row lengths, scan, long-row list, ranks
     int mcl_n = -1;
+    long long mcl_acc_key = -1;  // accumulator layout (stride, slots) whose arrays are known to be zero
     long long mcl_total = 0;
     void* pinned = nullptr;
     size_t pinned_n = 0;
@@ -1169,7 +1170,17 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     const long long bm_words = stride / 32;
     const int slots = (int)std::min<long long>(n, (long long)h->sms * 4);
     const size_t per = 8 * stride + 4 * stride + 4 * bm_words;
-    if (h->mcl_acc.n < per * slots) TSG_TRY(grow(h->mcl_acc, per * slots, st, true));
+    if (h->mcl_acc.n < per * slots) {
+        TSG_TRY(grow(h->mcl_acc, per * slots));
+        h->mcl_acc_key = -1;
+    }
+    // the kernel leaves the dense values and the bitmap zero after every row;
+    // a different n moves the regions, so they are cleared then
+    const long long key = stride * 4096 + slots;
+    if (h->mcl_acc_key != key) {
+        TSG_CHECK(cudaMemsetAsync(h->mcl_acc.p, 0, per * slots, st));
+        h->mcl_acc_key = key;
+    }
     char* acc = static_cast<char*>(h->mcl_acc.p);
     TSG_CHECK(cudaMemsetAsync(b + L.kept, 0, 4 * n, st));
     TSG_CHECK(cudaMemsetAsync(b + L.ctr, 0, 16, st));

@@ -116,3 +116,14 @@ def test_rmat_scale20_sampled_rows(tsg, handle):
     rp, _, val = got
     assert np.all(np.diff(rp) <= 1000) and np.all(np.diff(rp) >= 1)
     assert np.allclose(np.add.reduceat(val.astype(np.float64), rp[:-1]), 1.0, atol=1e-5)
+
+
+def test_handle_reused_across_graph_sizes(tsg, handle):
+    # one handle, graphs of three sizes in turn (larger, smaller, larger):
+    # the per-block accumulators move with the size and start from zero
+    for scale in (12, 10, 11):
+        Mt = gen.rmat_stochastic(scale=scale, edge_factor=16, seed=5)
+        R = tsg.mcl_step(tsg.DeviceCSR.from_host(Mt), topk=200, handle=handle)
+        torch.cuda.synchronize()
+        ref = oracle.mcl_step(Mt, topk=200, rows=np.arange(Mt.nrows))
+        compare_rows(R.to_host(), ref)
