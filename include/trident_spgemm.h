@@ -68,7 +68,7 @@ typedef enum {
     SPGEMM_ERR_HASH_OVERFLOW = 8,   /* an accumulator saw more entries than sized for */
     SPGEMM_ERR_NOT_CANONICAL = 9,   /* input failed validation */
     SPGEMM_ERR_INTERNAL = 10,       /* device consistency check failed */
-    SPGEMM_ERR_UNSUPPORTED = 11,    /* valid request this build does not handle */
+    SPGEMM_ERR_UNSUPPORTED = 11,    /* valid request the library does not handle */
     SPGEMM_ERR_CAPACITY = 12        /* an output buffer is smaller than the result */
 } spgemm_status;
 
