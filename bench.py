@@ -279,11 +279,8 @@ def run_native(args):
     launches = h.launch_count() - launches0
     h.set_timing(False)
     phase_ms, phase_cnt = h.read_timing()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 2 * prods / (ms * 1e-3) / 1e9
+    ms, all_prods = combine_over_ranks(ms, prods, "cuda")
+    value = 2 * all_prods / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel (numeric rows): algorithmic bytes per launch / duration
     num_bytes, sym_bytes = algorithmic_bytes(A, B, nnz)
@@ -371,6 +368,21 @@ def bench_single_pass(tsg, h, dA, dB, prods, nnz, steps, stream):
     return {"value": round(2 * prods / (ms * 1e-3) / 1e9, 2), "unit": UNIT, "ms_per_step": round(ms, 4),
             "numeric_fused_ms": round(phase_ms[3] / max(phase_cnt[3], 1), 4),
             "analysis_ms": round(phase_ms[0] / max(steps, 1), 4), "steps": steps}
+
+
+def combine_over_ranks(ms: float, units: float, device: str = "cpu"):
+    """(max of the ranks' step times, sum of the ranks' units): the job's
+    time is its slowest rank's, its work the work of all ranks.  One rank
+    (or no process group) returns its own values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def e2e_public_api(tsg, A, B, prods, args):
