@@ -335,8 +335,10 @@ spgemm_status spgemm_csr_transpose(spgemm_handle* h, spgemm_dtype dtype, const s
  * caller-allocated.  Y's rows come out sorted (X must have no repeated
  * column within a row).  Both maps are checked on the device to be
  * permutations before any entry of Y is written: SPGEMM_ERR_INVALID_ARG
- * otherwise (Y's row_ptr, col_idx and val then unspecified).  Synchronises
- * once (the check's result). */
+ * otherwise (Y's row_ptr, col_idx and val then unspecified).  With a column
+ * map, rows longer than 65536 entries are not re-sorted:
+ * SPGEMM_ERR_UNSUPPORTED (Y unspecified).  Synchronises once (the check's
+ * result). */
 spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X,
                                  const int32_t* row_perm, const int32_t* col_perm, spgemm_csr_out* Y,
                                  spgemm_stream_t stream);

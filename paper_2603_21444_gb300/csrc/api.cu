@@ -1033,6 +1033,10 @@ spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spg
         TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
         return SPGEMM_ERR_INVALID_ARG;
     }
+    if (status & kStatusCapacity) {  // a row too long to re-sort
+        TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
+        return SPGEMM_ERR_UNSUPPORTED;
+    }
     return SPGEMM_OK;
 }
 

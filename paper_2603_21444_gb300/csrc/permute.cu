@@ -23,6 +23,7 @@ namespace tsg {
 constexpr int kPermWarpMax = 1024;  // longest row one warp sorts on chip (8 KB of keys)
 constexpr int kPermWarps = 4;       // warps per block of the row kernel (32 KB of keys)
 constexpr int kPermLongThreads = 512;
+constexpr int kPermLongMax = 65536;  // longest row ranked (quadratic: ~10 ms per row at this length)
 
 __global__ void k_perm_hits(const int* __restrict__ perm, int n, int* hits, unsigned* status) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -117,13 +118,17 @@ __global__ void __launch_bounds__(kPermLongThreads) k_perm_long(const int* __res
                                                                 const int* __restrict__ yrp, int* ycol, T* yval,
                                                                 const int* long_count,
                                                                 const int* __restrict__ long_list, int* rank,
-                                                                const unsigned* status) {
+                                                                unsigned* status) {
     if (*status & kStatusBadMap) return;
     const int nl = *long_count;
     for (int l = blockIdx.x; l < nl; l += gridDim.x) {
         const int i = long_list[l];
         const int x0 = __ldg(rp + i), len = __ldg(rp + i + 1) - x0;
         const int dst = __ldg(yrp + (row_perm ? __ldg(row_perm + i) : i));
+        if (col_perm && len > kPermLongMax) {
+            if (threadIdx.x == 0) atomicOr(status, kStatusCapacity);
+            continue;
+        }
         if (!col_perm) {
             for (int e = threadIdx.x; e < len; e += blockDim.x) {
                 ycol[dst + e] = __ldg(col + x0 + e);

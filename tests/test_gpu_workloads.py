@@ -226,3 +226,20 @@ def test_split_then_deferred_product_same_handle(tsg, handle):
     torch.cuda.synchronize()
     ref, _ = oracle.spgemm(X, X)
     _same(C, ref)
+
+
+def test_permute_row_too_long_to_resort(tsg, handle):
+    from paper_2603_21444_gb300._abi import SpgemmError
+    n = 70000
+    rows = np.concatenate([np.zeros(n, dtype=np.int64), np.arange(1, 50)])
+    cols = np.concatenate([np.arange(n), np.arange(1, 50)])
+    X = gen.from_coo(50, n, rows, cols, np.ones(rows.size))
+    dX = tsg.DeviceCSR.from_host(X)
+    rp, cp, drp, dcp = _maps(50, n, 1, 2)
+    with pytest.raises(SpgemmError) as e:
+        tsg.permute(dX, drp, dcp, handle)
+    assert e.value.code == 11
+    # a row map alone needs no re-sort
+    Y = tsg.permute(dX, drp, None, handle)
+    torch.cuda.synchronize()
+    _same(Y, oracle.permute(X, rp, None))
