@@ -1316,8 +1316,8 @@ template <int CAP, typename T>
 struct WNumLayout {
     static constexpr int MAXA = CAP / 2;
     static constexpr int NBMAX = 2 * pow2floor_c(CAP);             // most buckets (a power of two)
-    static constexpr int cnt = 0;                                  // int[NBMAX + 4]
-    static constexpr int ocol = (NBMAX + 4) * 4;                   // int[CAP]
+    static constexpr int cnt = 0;                                  // u16[NBMAX + 8] counts, then starts
+    static constexpr int ocol = ((NBMAX + 8) * 2 + 15) & ~15;      // int[CAP]
     static constexpr int oval = ocol + 4 * CAP;                    // T[CAP]
     static constexpr int op = oval + (int)sizeof(T) * CAP;         // u16[CAP] product index
     static constexpr int oinst = op + 2 * CAP;                     // u8[CAP]
@@ -1336,7 +1336,8 @@ template <int PER, typename T, bool FUSED = false>
 __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* sm, const FusedRow* fr = nullptr) {
     constexpr int CAP = 32 * PER;
     using L = WNumLayout<CAP, T>;
-    int* cnt = reinterpret_cast<int*>(sm + L::cnt);
+    // bucket counts and starts never exceed CAP <= 512: 16 bits each
+    unsigned short* cnt = reinterpret_cast<unsigned short*>(sm + L::cnt);
     int* ocol = reinterpret_cast<int*>(sm + L::ocol);
     T* oval = reinterpret_cast<T*>(sm + L::oval);
     unsigned short* op = reinterpret_cast<unsigned short*>(sm + L::op);
@@ -1413,7 +1414,7 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     const int NB = min(2 * pow2ceil(u), L::NBMAX);
     Bucketer bk;
     bk.init(ncols, ncols_inv, NB);
-    for (int i = 4 * lane; i <= NB; i += 128) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
+    for (int i = 8 * lane; i <= NB; i += 256) *reinterpret_cast<int4*>(cnt + i) = make_int4(0, 0, 0, 0);
     // a row whose nnz equals its product count has no repeated column: it
     // only needs sorting (no tie-break, no run compaction)
     bool distinct = !FUSED && row_len == u;
@@ -1441,7 +1442,10 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
         int h = -1, b = 0;
         if (col[s] >= 0) {
             b = bk(col[s]);
-            h = atomicAdd(&cnt[b], 1);
+            // 32-bit atomic on the pair of 16-bit counters holding b
+            const unsigned half = (unsigned)(b & 1) << 4;
+            const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(cnt) + (b >> 1), 1u << half);
+            h = (int)((old >> half) & 0xffffu);
             hh[s] |= h;
         }
         const unsigned m = __ballot_sync(0xffffffffu, h == 1);
@@ -1451,38 +1455,44 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     __syncwarp();
 
     // the meta is dead from here on: the remaining arrays never alias
-    int* __restrict__ xcnt = cnt;
+    unsigned short* __restrict__ xcnt = cnt;
     int* __restrict__ xcol = ocol;
     T* __restrict__ xval = oval;
     unsigned short* __restrict__ xp = op;
     unsigned char* __restrict__ xinst = oinst;
     unsigned short* __restrict__ xwl = wl;
-    // ---- bucket starts: exclusive scan in rounds of 32 x 4 counters
+    // ---- bucket starts: exclusive scan in rounds of 32 x 8 counters
     {
         int base = 0;
-        for (int i0 = 0; i0 < NB; i0 += 128) {
-            const int i = i0 + 4 * lane;
+        for (int i0 = 0; i0 < NB; i0 += 256) {
+            const int i = i0 + 8 * lane;
             int4 v = make_int4(0, 0, 0, 0);
             if (i < NB) v = *reinterpret_cast<const int4*>(xcnt + i);
-            const int loc = v.x + v.y + v.z + v.w;
+            const unsigned w[4] = {(unsigned)v.x, (unsigned)v.y, (unsigned)v.z, (unsigned)v.w};
+            int loc = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) loc += (int)(w[k] & 0xffffu) + (int)(w[k] >> 16);
             int x = loc;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
-            int ex = base + x - loc;
+            unsigned ex = (unsigned)(base + x - loc);
             if (i < NB) {
-                int4 o;
-                o.x = ex; ex += v.x;
-                o.y = ex; ex += v.y;
-                o.z = ex; ex += v.z;
-                o.w = ex;
-                *reinterpret_cast<int4*>(xcnt + i) = o;
+                unsigned o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned lo = ex;
+                    ex += w[k] & 0xffffu;
+                    o[k] = lo | (ex << 16);
+                    ex += w[k] >> 16;
+                }
+                *reinterpret_cast<int4*>(xcnt + i) = make_int4((int)o[0], (int)o[1], (int)o[2], (int)o[3]);
             }
             base += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane == 0) xcnt[NB] = u;
+        if (lane == 0) xcnt[NB] = (unsigned short)u;
     }
     __syncwarp();
 
