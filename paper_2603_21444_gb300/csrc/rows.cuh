@@ -315,6 +315,114 @@ __device__ __forceinline__ void gather_chunks(const RowArgs& a, int ib, int nA, 
     }
 }
 
+// ------------------------------------------------- warp-team row meta
+//
+// Per A entry of the row (over the group's instances, instance by instance,
+// entries in stored order): its first product (prefix of the B-row
+// lengths), its B-row offset, a_ik (VALS) and its instance; nA and u for the
+// row.  Entries beyond MAXA are counted but not stored (the caller rejects
+// the row).  A row of several instances with at most 32 A entries in all
+// takes one round of loads -- lane t reads instance t's bounds, then lane L
+// its own A entry -- instead of one round of dependent loads per instance;
+// the entries keep the same order, so nothing downstream changes.
+template <bool VALS, typename T, int MAXA>
+__device__ __forceinline__ void warp_meta(const RowArgs& a, int ib, int icount, int rho, int lane, int* m_pre,
+                                          int* m_bs, T* m_a, unsigned char* m_inst, int& nA, int& u) {
+    nA = 0;
+    u = 0;
+    if (icount > 1 && icount <= 32) {
+        int ia0 = 0, ilen = 0;
+        if (lane < icount) {
+            const InstDev& I = a.inst[ib + lane];
+            if (a.merge) {
+                ilen = 1;
+            } else {
+                ia0 = __ldg(I.arp + rho);
+                ilen = __ldg(I.arp + rho + 1) - ia0;
+            }
+        }
+        int ix = ilen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ix, o);
+            if (lane >= o) ix += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, ix, 31);
+        if (total <= 32) {
+            int t = 0, e = 0;
+            for (int q = 0; q < icount; ++q) {
+                const int st = __shfl_sync(0xffffffffu, ix - ilen, q);
+                const int ln = __shfl_sync(0xffffffffu, ilen, q);
+                const int b0 = __shfl_sync(0xffffffffu, ia0, q);
+                if (lane >= st && lane < st + ln) {
+                    t = q;
+                    e = b0 + (lane - st);
+                }
+            }
+            const bool valid = lane < total;
+            int len = 0, bs = 0;
+            T av = T(1);
+            if (valid) {
+                const InstDev& I = a.inst[ib + t];
+                const int k = a.merge ? rho : __ldg(I.acol + e);
+                bs = __ldg(I.brp + k);
+                len = __ldg(I.brp + k + 1) - bs;
+                if (VALS && !a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
+            }
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (valid && lane < MAXA) {
+                m_pre[lane] = x - len;
+                m_bs[lane] = bs;
+                if (VALS) m_a[lane] = av;
+                m_inst[lane] = (unsigned char)t;
+            }
+            nA = total;
+            u = __shfl_sync(0xffffffffu, x, 31);
+            return;
+        }
+    }
+    for (int t = 0; t < icount; ++t) {
+        const InstDev& I = a.inst[ib + t];
+        int a0 = 0, a1 = 1;
+        if (!a.merge) {
+            a0 = __ldg(I.arp + rho);
+            a1 = __ldg(I.arp + rho + 1);
+        }
+        for (int e0 = a0; e0 < a1; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < a1;
+            int len = 0, bs = 0;
+            T av = T(1);
+            if (valid) {
+                const int k = a.merge ? rho : __ldg(I.acol + e);
+                bs = __ldg(I.brp + k);
+                len = __ldg(I.brp + k + 1) - bs;
+                if (VALS && !a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
+            }
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int idx = nA + lane;
+            if (valid && idx < MAXA) {
+                m_pre[idx] = u + x - len;
+                m_bs[idx] = bs;
+                if (VALS) m_a[idx] = av;
+                m_inst[idx] = (unsigned char)t;
+            }
+            nA += min(32, a1 - e0);
+            u += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+}
+
 // ------------------------------------------------- strided warp gather
 //
 // For rows of at most 32 A entries whose B rows are short, a chunk of 4
@@ -437,39 +545,8 @@ __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* s
     const int rho = (int)(unit - a.unit_base[g]);
     const int ib = G.inst_begin, icount = G.inst_count;
 
-    int nA = 0, u = 0;
-    for (int t = 0; t < icount; ++t) {
-        const InstDev& I = a.inst[ib + t];
-        int a0 = 0, a1 = 1;
-        if (!a.merge) {
-            a0 = __ldg(I.arp + rho);
-            a1 = __ldg(I.arp + rho + 1);
-        }
-        for (int e0 = a0; e0 < a1; e0 += 32) {
-            const int e = e0 + lane;
-            const bool valid = e < a1;
-            int len = 0, bs = 0;
-            if (valid) {
-                const int k = a.merge ? rho : __ldg(I.acol + e);
-                bs = __ldg(I.brp + k);
-                len = __ldg(I.brp + k + 1) - bs;
-            }
-            int x = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            const int idx = nA + lane;
-            if (valid && idx < L::MAXA) {
-                m_pre[idx] = u + x - len;
-                m_bs[idx] = bs;
-                m_inst[idx] = (unsigned char)t;
-            }
-            nA += min(32, a1 - e0);
-            u += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
+    int nA, u;
+    warp_meta<false, float, L::MAXA>(a, ib, icount, rho, lane, m_pre, m_bs, nullptr, m_inst, nA, u);
     if (nA > L::MAXA || u > CAP) {
         if (lane == 0) {
             atomicOr(a.status, kStatusInternal);
@@ -801,42 +878,8 @@ __device__ __forceinline__ void grouped_row_warp(const RowArgs& a, int unit, cha
     const int ib = G.inst_begin, icount = G.inst_count;
 
     // meta: first product, B-row offset, a_ik, instance per A entry
-    int nA = 0, u = 0;
-    for (int t = 0; t < icount; ++t) {
-        const InstDev& I = a.inst[ib + t];
-        int a0 = 0, a1 = 1;
-        if (!a.merge) {
-            a0 = __ldg(I.arp + rho);
-            a1 = __ldg(I.arp + rho + 1);
-        }
-        for (int e0 = a0; e0 < a1; e0 += 32) {
-            const int e = e0 + lane;
-            const bool valid = e < a1;
-            int len = 0, bs = 0;
-            T av = T(1);
-            if (valid) {
-                const int k = a.merge ? rho : __ldg(I.acol + e);
-                bs = __ldg(I.brp + k);
-                len = __ldg(I.brp + k + 1) - bs;
-                if (!a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
-            }
-            int x = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            const int idx = nA + lane;
-            if (valid && idx < kGroupedMaxA) {
-                m_pre[idx] = u + x - len;
-                m_bs[idx] = bs;
-                m_a[idx] = av;
-                m_inst[idx] = (unsigned char)t;
-            }
-            nA += min(32, a1 - e0);
-            u += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
+    int nA, u;
+    warp_meta<true, T, kGroupedMaxA>(a, ib, icount, rho, lane, m_pre, m_bs, m_a, m_inst, nA, u);
     if (nA > kGroupedMaxA || row_len > kGroupedMaxD || row_len <= 0) {
         if (lane == 0) atomicOr(a.status, kStatusInternal);
         __syncwarp();
@@ -1363,42 +1406,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
     const bool multi = a.merge || icount > 1;
 
     // ---- meta: B-row offset, a_ik, instance and prefix per A entry
-    int nA = 0, u = 0;
-    for (int t = 0; t < icount; ++t) {
-        const InstDev& I = a.inst[ib + t];
-        int a0 = 0, a1 = 1;
-        if (!a.merge) {
-            a0 = __ldg(I.arp + rho);
-            a1 = __ldg(I.arp + rho + 1);
-        }
-        for (int e0 = a0; e0 < a1; e0 += 32) {
-            const int e = e0 + lane;
-            const bool valid = e < a1;
-            int len = 0, bs = 0;
-            T av = T(1);
-            if (valid) {
-                const int k = a.merge ? rho : __ldg(I.acol + e);
-                bs = __ldg(I.brp + k);
-                len = __ldg(I.brp + k + 1) - bs;
-                if (!a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
-            }
-            int x = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            const int idx = nA + lane;
-            if (valid && idx < L::MAXA) {
-                m_pre[idx] = u + x - len;
-                m_bs[idx] = bs;
-                m_a[idx] = av;
-                m_inst[idx] = (unsigned char)t;
-            }
-            nA += min(32, a1 - e0);
-            u += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
+    int nA, u;
+    warp_meta<true, T, L::MAXA>(a, ib, icount, rho, lane, m_pre, m_bs, m_a, m_inst, nA, u);
     if (nA > L::MAXA || u > CAP) {
         if (lane == 0) atomicOr(a.status, kStatusInternal);
         if (FUSED) fused_offset(*fr, 0, a.status);  // the block and later tiles must not wait
