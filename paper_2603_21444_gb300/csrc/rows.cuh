@@ -661,6 +661,7 @@ constexpr int kThreadCap = 16;
 // (A entries, B-row bounds, every B row's first entry), so a row waits for
 // a few memory round trips instead of three per A entry.
 constexpr int kThreadBatch = 8;
+static_assert(kThreadBatch == 8, "the vector path below loads a batch as two groups of four");
 
 template <bool VALS, typename T>
 __device__ __forceinline__ int thread_gather(const RowArgs& a, const GroupDev& G, int rho, int* sc, T* sv,
@@ -678,13 +679,32 @@ __device__ __forceinline__ int thread_gather(const RowArgs& a, const GroupDev& G
         for (int e0 = a0; e0 < a1; e0 += kThreadBatch) {
             int kk[kThreadBatch], b0[kThreadBatch], len[kThreadBatch], c0[kThreadBatch];
             T av[kThreadBatch], v0[kThreadBatch];
+            // a whole batch at 16-byte boundaries: vector loads (a thread's
+            // entries are contiguous, so this cuts its L1 requests 4 x)
+            const bool vec = !a.merge && e0 + kThreadBatch <= a1 &&
+                             ((reinterpret_cast<uintptr_t>(I.acol + e0) & 15) == 0) &&
+                             (!VALS || (reinterpret_cast<uintptr_t>(aval + e0) & (4 * sizeof(T) - 1)) == 0);
+            if (vec) {
+                const int4 x0 = __ldg(reinterpret_cast<const int4*>(I.acol + e0));
+                const int4 x1 = __ldg(reinterpret_cast<const int4*>(I.acol + e0 + 4));
+                kk[0] = x0.x; kk[1] = x0.y; kk[2] = x0.z; kk[3] = x0.w;
+                kk[4] = x1.x; kk[5] = x1.y; kk[6] = x1.z; kk[7] = x1.w;
+                if (VALS) {
+                    Vec2<T>::load4(aval + e0, av);
+                    Vec2<T>::load4(aval + e0 + 4, av + 4);
+                } else {
 #pragma unroll
-            for (int e = 0; e < kThreadBatch; ++e) {
-                kk[e] = 0;
-                av[e] = T(1);
-                if (e0 + e < a1) {
-                    kk[e] = a.merge ? rho : __ldg(I.acol + e0 + e);
-                    if (VALS && !a.merge) av[e] = __ldg(aval + e0 + e);
+                    for (int e = 0; e < kThreadBatch; ++e) av[e] = T(1);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kThreadBatch; ++e) {
+                    kk[e] = 0;
+                    av[e] = T(1);
+                    if (e0 + e < a1) {
+                        kk[e] = a.merge ? rho : __ldg(I.acol + e0 + e);
+                        if (VALS && !a.merge) av[e] = __ldg(aval + e0 + e);
+                    }
                 }
             }
             int tot = 0;
