@@ -932,6 +932,15 @@ spgemm_status spgemm_trident_schedule(int32_t q, int32_t lambda, int32_t* a_tile
 
 namespace {
 
+// Bytes of transpose work for nc columns and nnz entries: column counts,
+// exclusive sums, scan partials, sort buffers.  The one formula both users
+// of h->tr size it with.
+size_t transpose_work_bytes(long long nc, long long nnz, size_t esz) {
+    const long long nblk = scan_blocks(std::max<long long>(nc, 1));
+    return align16(4 * std::max<long long>(nc, 1)) + align16(8 * (nc + 1)) + align16(8 * nblk) +
+           align16(4 * std::max<long long>(nnz, 1)) + align16(esz * std::max<long long>(nnz, 1));
+}
+
 // X^T into the given arrays, work from h->tr starting at byte offset `off`
 spgemm_status transpose_into(spgemm_handle* h, int dtype, const spgemm_csr_in* X, int* trp, int* tcol, void* tval,
                              size_t off, cudaStream_t st) {
@@ -942,7 +951,7 @@ spgemm_status transpose_into(spgemm_handle* h, int dtype, const spgemm_csr_in* X
     const size_t o_ex = o_work + align16(4 * std::max<long long>(nc, 1));
     const size_t o_bsum = o_ex + align16(8 * (nc + 1));
     const size_t o_tmp = o_bsum + align16(8 * nblk);
-    const size_t bytes = o_tmp + align16(4 * std::max<long long>(nnz, 1)) + align16(esz * std::max<long long>(nnz, 1));
+    const size_t bytes = off + transpose_work_bytes(nc, nnz, esz);
     TSG_TRY(grow(h->tr, bytes));
     char* b = static_cast<char*>(h->tr.p);
     PhaseScope ps(h, 6, st);
@@ -1081,11 +1090,9 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
         // the transpose may grow h->tr: compute pointers after it returns
         int* trp = nullptr;
         {
-            // grow first to the full size the transpose needs, then place A^T
-            const long long nblk = scan_blocks(std::max(A->ncols, 1));
-            const size_t need = o_work + align16(4 * std::max(A->ncols, 1)) + align16(8 * ((long long)A->ncols + 1)) +
-                                align16(8 * nblk) + align16(4 * nnz) + align16(esz * nnz);
-            TSG_TRY(grow(h->tr, need));
+            // grow first to the full size the transpose needs (so that it does
+            // not reallocate under the pointers below), then place A^T
+            TSG_TRY(grow(h->tr, o_work + transpose_work_bytes(A->ncols, A->nnz, esz)));
             char* b = static_cast<char*>(h->tr.p);
             trp = reinterpret_cast<int*>(b + o_rp);
             a.trp = trp;
