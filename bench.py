@@ -293,6 +293,12 @@ def run_native(args):
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": measured_traffic() if args.n_log2 == 20 and args.d == 16 else None,
             "peak_source": peak_kind, "algorithmic_bytes": num_bytes, "launch_ms": round(num_ms, 4)}
+    # streaming (per-product) model: every B-row gather misses cache -- 4 B
+    # per product in the symbolic pass, 4 + 8 B per product in the numeric one
+    stream_bytes = prods * (4 + 12)
+    roof["streaming_model"] = {"bytes_per_step": stream_bytes,
+                               "achieved_gbs": round(stream_bytes / (ms * 1e-3) / 1e9, 1),
+                               "frac": round(stream_bytes / (ms * 1e-3) / 1e9 / peak, 4)}
     phases = {"analysis_ms": phase_ms[0] / args.steps, "symbolic_rows_ms": sym_ms, "scan_ms": phase_ms[2] / args.steps,
               "numeric_rows_ms": num_ms, "heavy_ms": phase_ms[4] / args.steps,
               "symbolic_frac_of_hbm": round(sym_bytes / (sym_ms * 1e-3) / 1e9 / peak, 4) if sym_ms > 0 else None}
@@ -322,7 +328,7 @@ def run_native(args):
                 "single_pass": single, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if args.extras and world == 1:
             extras = {}
-            for name, fn in (("trident_grid", bench_trident), ("many_products", bench_many),
+            for name, fn in (("small_er", bench_small), ("trident_grid", bench_trident), ("many_products", bench_many),
                              ("autograd", bench_autograd), ("restriction", bench_restriction),
                              ("permutation", bench_permutation), ("markov_clustering", bench_mcl)):
                 try:
@@ -557,6 +563,43 @@ def bench_autograd(tsg, steps):
             "nnz_c": pat.C.nnz, "forward_ms": round(fwd_ms, 3), "forward_with_sizing_ms": round(fresh_ms, 3),
             "backward_ms": round(bwd_ms, 3), "backward_deterministic_ms": round(det_ms, 3),
             "fwd_plus_bwd_ms": round(fb_ms, 3), "forward_gflops": round(2 * prods / fwd_ms / 1e6, 2)}
+
+
+def bench_small(tsg, steps):
+    """The small ER case: C = A A, n = 4096, 8 per row, float64 -- launch
+    and latency bound, so reported in microseconds per call (symbolic +
+    numeric through the C ABI into a preallocated C)."""
+    import ctypes
+
+    import torch
+    import gen
+    from paper_2603_21444_gb300 import _abi
+    A = gen.er(4096, 4096, 8, 0)
+    prods = products(A, A)
+    dA = tsg.DeviceCSR.from_host(A)
+    h = tsg.Handle()
+    C = tsg.spgemm(dA, dA, h)
+    a_in, c_out = dA.as_in(), C.as_out()
+    box = ctypes.c_int64()
+    L = _abi.lib()
+    sptr = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        _abi.check(L.spgemm_symbolic(h.ptr, ctypes.byref(a_in), ctypes.byref(a_in), ctypes.c_void_p(c_out.row_ptr),
+                                     ctypes.byref(box), sptr), "symbolic")
+        _abi.check(L.spgemm_numeric(h.ptr, _abi.F64, ctypes.byref(a_in), ctypes.byref(a_in), ctypes.byref(c_out),
+                                    sptr), "numeric")
+
+    ms = _time(step, max(steps, 50), warmup=5)
+    # the same product sized once and replayed from a CUDA graph (numeric only)
+    plan = tsg.Plan([dA], [dA])
+    plan.execute(True)
+    ms_replay = _time(lambda: plan.execute(True), max(steps, 50), warmup=5)
+    plan.close()
+    h.close()
+    return {"workload": "ER A*A n=4096 d=8 f64 (seed 0)", "products": prods, "nnz_c": C.nnz,
+            "us_per_call": round(ms * 1e3, 2), "gflops": round(2 * prods / ms / 1e6, 2),
+            "plan_replay_us": round(ms_replay * 1e3, 2)}
 
 
 def bench_restriction(tsg, steps):
