@@ -633,7 +633,14 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 12 ? 256 : 512) : TEAM,
         sm = smem;
     }
     if constexpr (TEAM == 32) {
-        for (int i = begin + team; i < end; i += nteams) sym_row_warp<PER>(a, __ldg(a.list + i), sm);
+        // the next row's id is loaded before the current row starts
+        int i = begin + team;
+        int unit = i < end ? __ldg(a.list + i) : 0;
+        for (; i < end; i += nteams) {
+            const int next = i + nteams < end ? __ldg(a.list + i + nteams) : 0;
+            sym_row_warp<PER>(a, unit, sm);
+            unit = next;
+        }
     } else {
         for (int i = begin + team; i < end; i += nteams) sym_row<TEAM, PER>(a, __ldg(a.list + i), sm);
     }
