@@ -8,6 +8,17 @@ the whole product: analysis + symbolic + scan (+ nnz read back) + numeric.
 Metric: SpGEMM GFLOP/s = 2 x intermediate products / second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--n-log2 L] [--d D] [--no-cpu-baseline] [--no-e2e] [--no-extras]
+
+The JSON line carries the roofline of the numeric kernel (achieved
+algorithmic bytes per launch over its CUDA-event time, the measured peak,
+the DRAM traffic of the committed ncu capture while the kernel sources match
+it, and the per-product streaming model), the library's phase times, the
+oracle on the host cores (cpu_baseline), the same product end to end from
+pinned host memory (e2e), and, unless --no-extras, one line per further
+workload: the small ER case, the single-pass product, the trident grid, 256
+independent products, autograd, the restriction operator, the permuted
+banded matrix with its trident loads and volumes, and Markov clustering.
 
 Under torchrun (N > 1) every rank runs its own replica of the workload
 (independent problems, no collective on the data path); the time is the max
