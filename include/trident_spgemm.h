@@ -419,6 +419,30 @@ spgemm_status spgemm_device_status(spgemm_handle* h);
  * entries (host). */
 #define SPGEMM_NUM_PHASES 8
 spgemm_status spgemm_set_timing(spgemm_handle* h, int32_t enable);
+
+/* Workspace limit.  spgemm_set_workspace_limit caps the device bytes the
+ * handle's own workspace buffers may hold (bytes < 0: no cap, the default;
+ * a plan's private workspace is not counted).  A call whose workspace would
+ * grow past the cap returns SPGEMM_ERR_OOM before it allocates, leaving the
+ * buffers already held in place (the handle stays usable); a failing
+ * cudaMalloc gives the same code.  spgemm_workspace_bytes writes the bytes
+ * currently held (host int64).  Host only; SPGEMM_ERR_INVALID_ARG for a NULL
+ * handle or pointer. */
+spgemm_status spgemm_set_workspace_limit(spgemm_handle* h, int64_t bytes);
+spgemm_status spgemm_workspace_bytes(const spgemm_handle* h, int64_t* bytes);
+
+/* Fault injection for tests of the bounded device wait (the look-back of
+ * spgemm_fused's single pass; no other kernel of the library waits on
+ * another).  spin_limit > 0 caps the polls of one look-back wait (<= 0
+ * restores the default, 2^22 polls, seconds of waiting); hold_tile >= 0 makes
+ * that tile of rows (tile t = rows t*w .. t*w + w - 1, w the warps per block)
+ * never publish its count, so the next tile's wait runs out: the call then
+ * returns SPGEMM_ERR_DEVICE_TIMEOUT, the device stays usable and C is
+ * unspecified (every write still stays within capacity).  hold_tile = -1
+ * turns the injection off; a tile beyond the last one has no effect.
+ * SPGEMM_ERR_INVALID_ARG for hold_tile < -1.  Host only; applies to later
+ * calls on the handle. */
+spgemm_status spgemm_set_wait_test(spgemm_handle* h, int32_t spin_limit, int32_t hold_tile);
 spgemm_status spgemm_read_timing(spgemm_handle* h, double* ms, int64_t* count);
 
 #ifdef __cplusplus

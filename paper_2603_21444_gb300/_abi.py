@@ -94,6 +94,9 @@ SIGNATURES = {
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),
+    "spgemm_set_wait_test": ([P, I32, I32], ctypes.c_int),
+    "spgemm_set_workspace_limit": ([P, ctypes.c_int64], ctypes.c_int),
+    "spgemm_workspace_bytes": ([P, I64P], ctypes.c_int),
     "spgemm_read_timing": ([P, ctypes.POINTER(ctypes.c_double), I64P], ctypes.c_int),
 }
 

@@ -124,6 +124,25 @@ class Handle:
     def set_timing(self, on: bool):
         check(_abi.lib().spgemm_set_timing(self._h, 1 if on else 0), "spgemm_set_timing")
 
+    def set_workspace_limit(self, nbytes: int | None):
+        """Cap the device bytes this handle's workspace may hold (None: no
+        cap); a call that would grow past it raises SPGEMM_ERR_OOM."""
+        check(_abi.lib().spgemm_set_workspace_limit(self._h, -1 if nbytes is None else int(nbytes)),
+              "spgemm_set_workspace_limit")
+
+    def workspace_bytes(self) -> int:
+        """Device bytes the handle's workspace holds now."""
+        v = ctypes.c_int64()
+        check(_abi.lib().spgemm_workspace_bytes(self._h, ctypes.byref(v)), "spgemm_workspace_bytes")
+        return int(v.value)
+
+    def set_wait_test(self, spin_limit: int = 0, hold_tile: int = -1):
+        """Fault injection for the bounded look-back wait of the single-pass
+        product: cap its polls at spin_limit (0: default) and withhold the
+        entry of tile hold_tile (-1: none), which makes that call raise
+        SPGEMM_ERR_DEVICE_TIMEOUT."""
+        check(_abi.lib().spgemm_set_wait_test(self._h, int(spin_limit), int(hold_tile)), "spgemm_set_wait_test")
+
     def read_timing(self):
         """(ms per phase, intervals per phase) since the last read."""
         ms = (ctypes.c_double * _abi.NUM_PHASES)()

@@ -75,6 +75,9 @@ struct spgemm_handle {
     std::vector<int> plan_hist;
     int64_t launches = 0;
     bool timing = false;
+    long long ws_limit = -1;              // cap on the device bytes held by the buffers above (-1: none)
+    int wait_limit = kLookbackSpinLimit;  // polls of a look-back wait of the single-pass product
+    int hold_tile = -1;                   // fault injection: a look-back entry never published
     std::vector<PhaseEvent> pending;
     std::vector<cudaEvent_t> spare;
     cudaStream_t last_stream = nullptr;
@@ -108,15 +111,26 @@ spgemm_status cuda_status(cudaError_t e) {
         if (s_ != SPGEMM_OK) return s_;                   \
     } while (0)
 
-spgemm_status grow(DevBuf& b, size_t bytes, cudaStream_t zero_on = nullptr, bool zero = false) {
+// Device bytes the handle's workspace buffers hold.
+size_t held_bytes(const spgemm_handle* h) {
+    return h->units.n + h->small.n + h->dense.n + h->status.n + h->tr.n + h->mcl.n + h->mcl_acc.n + h->perm.n;
+}
+
+// Grows b (one of h's buffers, or a buffer that will replace one) to at
+// least `bytes`.  A growth that would take the bytes held over the handle's
+// workspace limit returns SPGEMM_ERR_OOM and leaves b as it was; a failed
+// cudaMalloc returns SPGEMM_ERR_OOM with b empty.
+spgemm_status grow(spgemm_handle* h, DevBuf& b, size_t bytes, cudaStream_t zero_on = nullptr, bool zero = false) {
     if (b.n >= bytes) return SPGEMM_OK;
+    const size_t want = std::max(bytes, size_t(1) << 16);
+    if (h->ws_limit >= 0 && held_bytes(h) - b.n + want > (size_t)h->ws_limit) return SPGEMM_ERR_OOM;
     if (b.p) {
         cudaError_t e = cudaFree(b.p);
         b.p = nullptr;
         b.n = 0;
         if (e != cudaSuccess) return cuda_status(e);
     }
-    size_t n = std::max(bytes, size_t(1) << 16);
+    const size_t n = want;
     if (cudaMalloc(&b.p, n) != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -305,9 +319,11 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
 
     // ---- workspace
     if (U > h->units_cap) {
-        TSG_TRY(grow(h->units, units_bytes(U)));
-        h->units_cap = U;
+        // a failed growth may leave the buffer empty: units_cap follows it
+        h->units_cap = h->units.n >= units_bytes(U) ? h->units_cap : -1;
         h->plan_valid = false;
+        TSG_TRY(grow(h, h->units, units_bytes(U)));
+        h->units_cap = U;
     }
     char* ub = static_cast<char*>(h->units.p);
     unsigned char* d_bin_of = reinterpret_cast<unsigned char*>(ub);
@@ -334,13 +350,13 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         h->plan_valid = false;
         h->last_stage_dst = nullptr;
     }
-    TSG_TRY(grow(h->small, small_bytes));
+    TSG_TRY(grow(h, h->small, small_bytes));
     char* sb = static_cast<char*>(h->small.p);
     int* d_hist = reinterpret_cast<int*>(sb + o_hist);
     int* d_off = reinterpret_cast<int*>(sb + o_off);
     int* d_cur = reinterpret_cast<int*>(sb + o_cur);
     int* d_tick = reinterpret_cast<int*>(sb + o_tick);
-    TSG_TRY(grow(h->status, 16, st, true));
+    TSG_TRY(grow(h, h->status, 16, st, true));
     unsigned* d_status = static_cast<unsigned*>(h->status.p);
     long long* d_bsum = reinterpret_cast<long long*>(sb + o_bsum);
     long long* d_nnz = reinterpret_cast<long long*>(sb + o_nnz);
@@ -474,6 +490,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         fc.cap = fused_cap;
         fc.nunits = (int)U;
         fc.crp = groups[0].crp;
+        fc.spin_limit = h->wait_limit;
+        fc.hold_tile = h->hold_tile;
         const int occ = std::max(1, num_fused_blocks_per_sm(v, dtype, wv));
         const int blocks = (int)std::min<long long>(ntiles, (long long)h->sms * occ);
         {
@@ -553,7 +571,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         PhaseScope ps(h, 4, st);
         const int blocks = std::min(hist[nb], h->sms);
         const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
-        TSG_TRY(grow(h->dense, (size_t)blocks * chunk * esz, st, true));
+        TSG_TRY(grow(h, h->dense, (size_t)blocks * chunk * esz, st, true));
         // blocks beyond the allocation would share slots: size the grid to it
         const int slots = (int)std::min<size_t>(blocks, h->dense.n / ((size_t)chunk * esz));
         la.bin = nb;
@@ -858,7 +876,8 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
         return SPGEMM_OK;
     }
     if (U > h->units_cap) {
-        TSG_TRY(grow(h->units, units_bytes(U)));
+        h->units_cap = h->units.n >= units_bytes(U) ? h->units_cap : -1;
+        TSG_TRY(grow(h, h->units, units_bytes(U)));
         h->units_cap = U;
     }
     char* ub = static_cast<char*>(h->units.p);
@@ -873,7 +892,7 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
     size_t o_rb = o_tg + align16(sizeof(GroupDev) * nt);
     size_t o_cb = o_rb + align16(4 * (nrp + 1));
     size_t bytes = o_cb + align16(4 * (ncp + 1));
-    TSG_TRY(grow(h->small, bytes));
+    TSG_TRY(grow(h, h->small, bytes));
     h->last_stage_dst = nullptr;
     char* sb = static_cast<char*>(h->small.p);
     std::vector<char> stage(bytes - o_ubase);
@@ -952,7 +971,7 @@ spgemm_status transpose_into(spgemm_handle* h, int dtype, const spgemm_csr_in* X
     const size_t o_bsum = o_ex + align16(8 * (nc + 1));
     const size_t o_tmp = o_bsum + align16(8 * nblk);
     const size_t bytes = off + transpose_work_bytes(nc, nnz, esz);
-    TSG_TRY(grow(h->tr, bytes));
+    TSG_TRY(grow(h, h->tr, bytes));
     char* b = static_cast<char*>(h->tr.p);
     PhaseScope ps(h, 6, st);
     TSG_CHECK(launch_transpose(dtype, X->row_ptr, X->col_idx, X->val, X->nrows, X->ncols, nnz, trp, tcol, tval,
@@ -1004,8 +1023,8 @@ spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spg
     const size_t o_list = o_ex + align16(8 * (nr + 1));
     const size_t o_rank = o_list + align16(4 * std::max<long long>(nr, 1));
     const size_t bytes = o_rank + align16(4 * std::max<long long>(nnz, 1));
-    TSG_TRY(grow(h->perm, bytes));
-    TSG_TRY(grow(h->status, 16, st, true));
+    TSG_TRY(grow(h, h->perm, bytes));
+    TSG_TRY(grow(h, h->status, 16, st, true));
     char* b = static_cast<char*>(h->perm.p);
     unsigned* d_status = static_cast<unsigned*>(h->status.p);
     PhaseScope ps(h, 6, st);
@@ -1060,7 +1079,7 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
     if (dev != h->device) return SPGEMM_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     note_stream(h, st);
-    TSG_TRY(grow(h->status, 16, st, true));
+    TSG_TRY(grow(h, h->status, 16, st, true));
     BwdArgs a{};
     a.m = A->nrows;
     a.kdim = B->nrows;
@@ -1086,13 +1105,13 @@ spgemm_status spgemm_backward(spgemm_handle* h, spgemm_dtype dtype, const spgemm
         const size_t o_col = o_rp + align16(4 * ((long long)A->ncols + 1));
         const size_t o_val = o_col + align16(4 * nnz);
         const size_t o_work = o_val + align16(esz * nnz);
-        TSG_TRY(grow(h->tr, o_work + 16));
+        TSG_TRY(grow(h, h->tr, o_work + 16));
         // the transpose may grow h->tr: compute pointers after it returns
         int* trp = nullptr;
         {
             // grow first to the full size the transpose needs (so that it does
             // not reallocate under the pointers below), then place A^T
-            TSG_TRY(grow(h->tr, o_work + transpose_work_bytes(A->ncols, A->nnz, esz)));
+            TSG_TRY(grow(h, h->tr, o_work + transpose_work_bytes(A->ncols, A->nnz, esz)));
             char* b = static_cast<char*>(h->tr.p);
             trp = reinterpret_cast<int*>(b + o_rp);
             a.trp = trp;
@@ -1151,12 +1170,12 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
         return SPGEMM_OK;
     }
     if ((long long)prm->topk * n > (1ll << 31) - 1) return SPGEMM_ERR_INDEX_OVERFLOW;
-    TSG_TRY(grow(h->status, 16, st, true));
+    TSG_TRY(grow(h, h->status, 16, st, true));
     TSG_TRY(grow_pinned(h, 64));
     long long* p_ll = static_cast<long long*>(h->pinned);
     // 1. per-row bound min(products, topk) and its exclusive sums
     MclLayout L0 = mcl_layout(n, 1);
-    TSG_TRY(grow(h->mcl, L0.bytes));
+    TSG_TRY(grow(h, h->mcl, L0.bytes));
     char* b = static_cast<char*>(h->mcl.p);
     PhaseScope ps(h, 7, st);
     TSG_CHECK(launch_mcl_bounds(Mt->row_ptr, Mt->col_idx, (int)n, prm->topk, reinterpret_cast<int*>(b + L0.ub), st));
@@ -1169,7 +1188,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     if (h->mcl.n < L.bytes) {
         // keep the bounds already computed while growing
         DevBuf nb;
-        TSG_TRY(grow(nb, L.bytes));
+        TSG_TRY(grow(h, nb, L.bytes));
         TSG_CHECK(cudaMemcpyAsync(nb.p, h->mcl.p, L0.tmp_col, cudaMemcpyDeviceToDevice, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         cudaFree(h->mcl.p);
@@ -1182,7 +1201,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     const int slots = (int)std::min<long long>(n, (long long)h->sms * 4);
     const size_t per = 8 * stride + 4 * stride + 4 * bm_words;
     if (h->mcl_acc.n < per * slots) {
-        TSG_TRY(grow(h->mcl_acc, per * slots));
+        TSG_TRY(grow(h, h->mcl_acc, per * slots));
         h->mcl_acc_key = -1;
     }
     // the kernel leaves the dense values and the bitmap zero after every row;
@@ -1267,6 +1286,26 @@ spgemm_status spgemm_device_status(spgemm_handle* h) {
     if (st & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
     if (st & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;
     if (st & kStatusInternal) return SPGEMM_ERR_INTERNAL;
+    if (st & kStatusTimeout) return SPGEMM_ERR_DEVICE_TIMEOUT;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_set_workspace_limit(spgemm_handle* h, int64_t bytes) {
+    if (!h) return SPGEMM_ERR_INVALID_ARG;
+    h->ws_limit = bytes < 0 ? -1 : bytes;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_workspace_bytes(const spgemm_handle* h, int64_t* bytes) {
+    if (!h || !bytes) return SPGEMM_ERR_INVALID_ARG;
+    *bytes = (int64_t)held_bytes(h);
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_set_wait_test(spgemm_handle* h, int32_t spin_limit, int32_t hold_tile) {
+    if (!h || hold_tile < -1) return SPGEMM_ERR_INVALID_ARG;
+    h->wait_limit = spin_limit > 0 ? spin_limit : kLookbackSpinLimit;
+    h->hold_tile = hold_tile;
     return SPGEMM_OK;
 }
 

@@ -75,12 +75,16 @@ enum : unsigned {
 };
 
 // single-pass product: ticket counter and look-back state (rows.cuh)
+constexpr int kLookbackSpinLimit = 1 << 22;  // default cap on the polls of one look-back wait
+
 struct FusedCtl {
     int* ticket;                 // next tile of rows to hand out
     unsigned long long* lb;      // per tile: flag << 62 | value
     long long cap;               // entries the output can hold
     int nunits;                  // rows
     int* crp;                    // output row_ptr (nunits + 1)
+    int spin_limit;              // polls a look-back makes before it reports a timeout
+    int hold_tile;               // fault injection: this tile never publishes its entry (-1: none)
 };
 
 // ------------------------------------------------------------------- helpers

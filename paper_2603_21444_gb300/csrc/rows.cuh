@@ -1269,11 +1269,12 @@ __device__ __forceinline__ void num_row(const RowArgs& a, int unit, char* sm) {
 // published values until it meets an inclusive prefix (flag 2), then
 // publishes its own inclusive prefix.  Every earlier tile belongs to a
 // running block (tickets go only to running blocks), so the walk ends; a
-// bounded spin turns a stall into an error instead.  One entry per tile
+// bounded spin turns a stall into an error instead: after fc.spin_limit polls
+// the wait sets kStatusTimeout and the tile publishes the partial sum it has,
+// so later tiles do not wait on it in turn (their offsets are then wrong, but
+// every write stays checked against the output's capacity).  One entry per tile
 // rather than per row keeps the walks short: per-row entries arrive faster
 // than a walk of 32 entries per memory round trip can follow.
-
-constexpr int kLookbackSpinLimit = 1 << 22;
 
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -1296,7 +1297,8 @@ constexpr int kLookbackPer = 4;  // entries read per lane and round: a window of
 // one 64-bit word carrying its flag with its value, so relaxed loads suffice.
 __device__ __forceinline__ long long lookback_offset(const FusedCtl& fc, int t, long long c, unsigned* status) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) st_release_u64(fc.lb + t, (1ull << 62) | (unsigned long long)c);
+    const bool publish = t != fc.hold_tile;
+    if (lane == 0 && publish) st_release_u64(fc.lb + t, (1ull << 62) | (unsigned long long)c);
     long long excl = 0;
     int j = t - 1, spins = 0;
     while (j >= 0) {
@@ -1318,7 +1320,7 @@ __device__ __forceinline__ long long lookback_offset(const FusedCtl& fc, int t, 
             wait = wait || (none & need[k]) != 0;
         }
         if (wait) {
-            if (++spins > kLookbackSpinLimit) {
+            if (++spins > fc.spin_limit) {
                 if (lane == 0) atomicOr(status, kStatusTimeout);
                 break;
             }
@@ -1335,7 +1337,7 @@ __device__ __forceinline__ long long lookback_offset(const FusedCtl& fc, int t, 
         if (found) break;
         j -= 32 * kLookbackPer;
     }
-    if (lane == 0) st_release_u64(fc.lb + t, (2ull << 62) | (unsigned long long)(excl + c));
+    if (lane == 0 && publish) st_release_u64(fc.lb + t, (2ull << 62) | (unsigned long long)(excl + c));
     return excl;
 }
 

@@ -61,6 +61,9 @@ def test_null_handle_rejected(lib):
     assert lib.spgemm_numeric(None, 1, None, None, None, None) == 1
     assert lib.spgemm_merge(None, 1, 1, None, None, None, None) == 1
     assert lib.spgemm_batched(None, 1, 1, None, None, 1, None, None, None, None, None) == 1
+    assert lib.spgemm_set_wait_test(None, 1, 0) == 1
+    assert lib.spgemm_set_workspace_limit(None, 0) == 1
+    assert lib.spgemm_workspace_bytes(None, None) == 1
 
 
 def test_create_without_device_reports_cuda_error(lib):

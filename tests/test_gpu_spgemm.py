@@ -279,6 +279,55 @@ def test_single_pass_capacity_error(tsg, handle):
     assert_matches(_fused(tsg, A, A, handle), A, A)
 
 
+@pytest.mark.parametrize("spin_limit", [1, 1000])
+def test_single_pass_bounded_wait_reports_timeout(tsg, handle, spin_limit):
+    # injected on the host: tile 0 of the single pass never publishes its
+    # look-back entry, so tile 1's wait runs out after spin_limit polls; the
+    # call reports SPGEMM_ERR_DEVICE_TIMEOUT and the device stays usable
+    from paper_2603_21444_gb300._abi import SpgemmError
+    A = gen.er(4096, 4096, 8, 0)
+    handle.set_wait_test(spin_limit, 0)
+    with pytest.raises(SpgemmError) as e:
+        _fused(tsg, A, A, handle)
+    assert e.value.code == 7
+    # a held tile beyond the last one changes nothing (default cap: with a
+    # cap of a few polls an ordinary wait on a tile still being computed
+    # could run out too)
+    handle.set_wait_test(0, 1 << 30)
+    assert_matches(_fused(tsg, A, A, handle), A, A)
+    handle.set_wait_test()
+    assert_matches(_fused(tsg, A, A, handle), A, A)
+    with pytest.raises(SpgemmError) as e:
+        handle.set_wait_test(0, -2)
+    assert e.value.code == 1
+
+
+def test_workspace_limit_reports_oom_and_recovers(tsg, handle):
+    # allocation failure injected on the host: a call whose workspace would
+    # grow past the handle's cap reports SPGEMM_ERR_OOM before allocating,
+    # keeps the buffers it holds, and the handle stays usable and exact
+    from paper_2603_21444_gb300._abi import SpgemmError
+    A = gen.er(4096, 4096, 8, 0)
+    handle.set_workspace_limit(0)
+    with pytest.raises(SpgemmError) as e:
+        run_product(tsg, A, A, handle)
+    assert e.value.code == 5
+    handle.set_workspace_limit(None)
+    assert_matches(run_product(tsg, A, A, handle), A, A)
+    held = handle.workspace_bytes()
+    assert held > 0
+    handle.set_workspace_limit(held)
+    assert_matches(run_product(tsg, A, A, handle), A, A)  # fits in what is held
+    A2 = gen.er(1 << 15, 1 << 15, 8, 1)
+    with pytest.raises(SpgemmError) as e:
+        run_product(tsg, A2, A2, handle)
+    assert e.value.code == 5
+    assert handle.workspace_bytes() == held
+    assert_matches(run_product(tsg, A, A, handle), A, A)
+    handle.set_workspace_limit(None)
+    assert_matches(run_product(tsg, A2, A2, handle), A2, A2)
+
+
 def test_single_pass_full_size_matches_two_pass(tsg, handle):
     n, d = 1 << 20, 16
     A = gen.er(n, n, d, 0)
