@@ -257,6 +257,36 @@ spgemm_status spgemm_plan_execute(spgemm_plan* p, const spgemm_csr_out* C, int32
                                   spgemm_stream_t stream);
 spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spgemm_stream_t stream,
                                    spgemm_tune* chosen);
+
+/* Persistent autotune cache (host only).  The layouts spgemm_plan_autotune
+ * chooses are kept per process, keyed by the GPU model (compute capability
+ * and SM count), the dtype and the shape of the product-count histogram
+ * (log2 of every bin's row count).  A cache file makes them outlive the
+ * process: a text file, one entry per line,
+ *     tsg-tune-1 <key: 16 hex digits> <num_bins> <warps_per_block>
+ *                <sym_warps_per_block> then <bin_upper bin_kernel> per bin
+ * spgemm_tune_cache_open(path, *loaded): takes the file's entries into the
+ * process's cache (a later line replaces an earlier one with the same key;
+ * lines that do not parse or fail the spgemm_set_tune checks are skipped)
+ * and appends every later choice to it (one write per line, so processes
+ * may share the file).  path NULL: the file named by the environment
+ * variable TRIDENT_SPGEMM_TUNE_CACHE, else none.  A missing file counts as
+ * empty and is created on the first append.  Without an open call the first
+ * spgemm_plan_autotune reads the environment variable itself.  *loaded (may
+ * be NULL) receives the entries taken.  SPGEMM_ERR_INVALID_ARG if the file
+ * exists but cannot be read; spgemm_plan_autotune returns the same code when
+ * it cannot append (the plan keeps the layout it chose).
+ * spgemm_tune_cache_clear: empties the process's cache and detaches the
+ * file (the file is not changed).
+ * spgemm_tune_cache_store: records a layout under a key (checked as by
+ * spgemm_set_tune) and appends it to the file, if one is open.
+ * spgemm_tune_cache_count / _entry: the number of entries, and entry
+ * `index` (0 <= index < count, in key order). */
+spgemm_status spgemm_tune_cache_open(const char* path, int64_t* loaded);
+spgemm_status spgemm_tune_cache_clear(void);
+spgemm_status spgemm_tune_cache_store(uint64_t key, const spgemm_tune* t);
+spgemm_status spgemm_tune_cache_count(int64_t* n);
+spgemm_status spgemm_tune_cache_entry(int64_t index, uint64_t* key, spgemm_tune* t);
 spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count);
 spgemm_status spgemm_plan_destroy(spgemm_plan* p);
 

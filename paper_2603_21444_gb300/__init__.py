@@ -7,4 +7,5 @@ in include/trident_spgemm.h.  PyTorch supplies device memory and streams.
 """
 from .api import (BatchPlan, DeviceCSR, Handle, Plan, TridentPlan, batched, default_handle, default_tune,  # noqa: F401
                   fused_into, mcl_step, merge, numeric_into, permute, products, spgemm, spgemm_single_pass, symbolic,
-                  tile_split, trident_bounds, trident_loads, trident_schedule)
+                  tile_split, trident_bounds, trident_loads, trident_schedule, tune_cache_clear, tune_cache_entries,
+                  tune_cache_open, tune_cache_store)

@@ -87,6 +87,11 @@ SIGNATURES = {
     "spgemm_plan_execute": ([P, ctypes.POINTER(CsrOut), I32, P], ctypes.c_int),
     "spgemm_plan_autotune": ([P, ctypes.POINTER(CsrOut), P, ctypes.POINTER(Tune)], ctypes.c_int),
     "spgemm_plan_launch_count": ([P, I64P], ctypes.c_int),
+    "spgemm_tune_cache_open": ([ctypes.c_char_p, I64P], ctypes.c_int),
+    "spgemm_tune_cache_clear": ([], ctypes.c_int),
+    "spgemm_tune_cache_store": ([ctypes.c_uint64, ctypes.POINTER(Tune)], ctypes.c_int),
+    "spgemm_tune_cache_count": ([I64P], ctypes.c_int),
+    "spgemm_tune_cache_entry": ([ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Tune)], ctypes.c_int),
     "spgemm_plan_destroy": ([P], ctypes.c_int),
     "spgemm_csr_transpose_noalloc": ([ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_mcl_expand": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(MclParams), P, I64P, P], ctypes.c_int),

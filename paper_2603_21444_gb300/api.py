@@ -7,6 +7,7 @@ GPU and the built library these functions raise.
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -419,6 +420,38 @@ def trident_schedule(q: int, lam: int):
     gp = (ctypes.c_int32 * (q * q * lam + 1))()
     check(_abi.lib().spgemm_trident_schedule(q, lam, a, b, gp), "spgemm_trident_schedule")
     return list(a), list(b), list(gp)
+
+
+def tune_cache_open(path: str | None = None) -> int:
+    """Take the entries of a persistent autotune cache file into the process's
+    cache and append later autotune choices to it (path None: the file named
+    by TRIDENT_SPGEMM_TUNE_CACHE, else none).  Returns the entries taken."""
+    n = ctypes.c_int64()
+    check(_abi.lib().spgemm_tune_cache_open(None if path is None else os.fsencode(path), ctypes.byref(n)),
+          "spgemm_tune_cache_open")
+    return int(n.value)
+
+
+def tune_cache_clear():
+    """Empty the process's autotune cache and detach its file."""
+    check(_abi.lib().spgemm_tune_cache_clear(), "spgemm_tune_cache_clear")
+
+
+def tune_cache_store(key: int, tune: Tune):
+    """Record a layout under a key (appended to the open cache file, if any)."""
+    check(_abi.lib().spgemm_tune_cache_store(ctypes.c_uint64(key), ctypes.byref(tune)), "spgemm_tune_cache_store")
+
+
+def tune_cache_entries() -> list[tuple[int, Tune]]:
+    """(key, layout) of every entry of the process's autotune cache, in key order."""
+    n = ctypes.c_int64()
+    check(_abi.lib().spgemm_tune_cache_count(ctypes.byref(n)), "spgemm_tune_cache_count")
+    out = []
+    for i in range(n.value):
+        k, t = ctypes.c_uint64(), Tune()
+        check(_abi.lib().spgemm_tune_cache_entry(i, ctypes.byref(k), ctypes.byref(t)), "spgemm_tune_cache_entry")
+        out.append((int(k.value), t))
+    return out
 
 
 class Plan:

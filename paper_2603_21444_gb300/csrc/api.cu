@@ -1344,8 +1344,16 @@ spgemm_status spgemm_read_timing(spgemm_handle* h, double* ms, int64_t* count) {
 
 // ===================================================================== plans
 
+#include <fcntl.h>
+#include <unistd.h>
+
+#include <cerrno>
+#include <cstdio>
+#include <cstdlib>
+#include <iterator>
 #include <map>
 #include <mutex>
+#include <string>
 
 struct spgemm_plan {
     spgemm_handle* h = nullptr;  // private workspace
@@ -1363,6 +1371,110 @@ namespace {
 
 std::mutex g_tune_mu;
 std::map<uint64_t, spgemm_tune> g_tune_cache;
+
+// ---- persistent autotune cache
+//
+// A text file, one chosen layout per line:
+//   tsg-tune-1 <key, 16 hex digits> <num_bins> <warps_per_block>
+//              <sym_warps_per_block> <bin_upper[b] bin_kernel[b]> x num_bins
+// The key hashes the GPU model (compute capability, SM count), the dtype and
+// the shape of the product-count histogram, so an entry applies on any GPU of
+// the same model.  Entries are appended (one write per line); on reading,
+// lines that do not parse or whose layout fails check_tune are skipped and a
+// later line replaces an earlier one with the same key.
+constexpr const char* kTuneTag = "tsg-tune-1";
+constexpr const char* kTuneEnv = "TRIDENT_SPGEMM_TUNE_CACHE";
+std::string g_tune_path;      // file chosen layouts are appended to ("" = none)
+bool g_tune_env_done = false;  // the environment variable has been looked at
+
+bool parse_tune_line(const char* line, uint64_t* key, spgemm_tune* t) {
+    char tag[16] = {0};
+    unsigned long long k = 0;
+    int nb = 0, wpb = 0, swpb = 0, used = 0;
+    if (std::sscanf(line, "%15s %16llx %d %d %d%n", tag, &k, &nb, &wpb, &swpb, &used) != 5) return false;
+    if (std::strcmp(tag, kTuneTag) != 0 || nb < 1 || nb > SPGEMM_MAX_BINS) return false;
+    spgemm_tune x;
+    default_tune(&x);
+    x.num_bins = nb;
+    x.warps_per_block = wpb;
+    x.sym_warps_per_block = swpb;
+    x.validate = 0;
+    const char* q = line + used;
+    for (int b = 0; b < nb; ++b) {
+        int n = 0;
+        if (std::sscanf(q, "%d %d%n", &x.bin_upper[b], &x.bin_kernel[b], &n) != 2) return false;
+        q += n;
+    }
+    while (*q == ' ' || *q == '\t' || *q == '\r' || *q == '\n') ++q;
+    if (*q != '\0' || check_tune(&x) != SPGEMM_OK) return false;
+    *key = (uint64_t)k;
+    *t = x;
+    return true;
+}
+
+std::string format_tune_line(uint64_t key, const spgemm_tune& t) {
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), "%s %016llx %d %d %d", kTuneTag, (unsigned long long)key, t.num_bins,
+                  t.warps_per_block, t.sym_warps_per_block);
+    std::string line = buf;
+    for (int b = 0; b < t.num_bins; ++b) {
+        std::snprintf(buf, sizeof(buf), " %d %d", t.bin_upper[b], t.bin_kernel[b]);
+        line += buf;
+    }
+    return line + "\n";
+}
+
+// Adds the file's entries to the cache (caller holds g_tune_mu); returns the
+// number taken, or -1 if the file exists but cannot be read.
+long long load_tune_file_locked(const std::string& path) {
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return errno == ENOENT ? 0 : -1;
+    long long n = 0;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        const size_t len = std::strlen(line);
+        if (len + 1 == sizeof(line) && line[len - 1] != '\n') {
+            // longer than any valid entry: skip the rest of it
+            int c;
+            while ((c = std::fgetc(f)) != EOF && c != '\n') {
+            }
+            continue;
+        }
+        uint64_t key;
+        spgemm_tune t;
+        if (parse_tune_line(line, &key, &t)) {
+            g_tune_cache[key] = t;
+            ++n;
+        }
+    }
+    const bool bad = std::ferror(f) != 0;  // e.g. the path names a directory
+    std::fclose(f);
+    return bad ? -1 : n;
+}
+
+void tune_env_locked() {
+    if (g_tune_env_done) return;
+    g_tune_env_done = true;
+    const char* env = std::getenv(kTuneEnv);
+    if (env && *env) {
+        g_tune_path = env;
+        load_tune_file_locked(g_tune_path);
+    }
+}
+
+// Records a chosen layout in the cache and appends it to the file, if any
+// (caller holds g_tune_mu).  SPGEMM_ERR_INVALID_ARG if the file cannot be
+// written.
+spgemm_status store_tune_locked(uint64_t key, const spgemm_tune& t) {
+    g_tune_cache[key] = t;
+    if (g_tune_path.empty()) return SPGEMM_OK;
+    const std::string line = format_tune_line(key, t);
+    const int fd = ::open(g_tune_path.c_str(), O_WRONLY | O_CREAT | O_APPEND, 0644);
+    if (fd < 0) return SPGEMM_ERR_INVALID_ARG;
+    const ssize_t w = ::write(fd, line.data(), line.size());
+    ::close(fd);
+    return w == (ssize_t)line.size() ? SPGEMM_OK : SPGEMM_ERR_INVALID_ARG;
+}
 
 spgemm_status plan_bind(spgemm_plan* p, const spgemm_csr_out* C, std::vector<const void*>* key) {
     key->clear();
@@ -1504,12 +1616,14 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
     std::vector<const void*> key;
     TSG_TRY(plan_bind(p, C, &key));
     plan_drop_graph(p);
-    // cache key: device, dtype, the problem's product-count histogram
+    // cache key: GPU model, dtype, the problem's product-count histogram
     TSG_TRY(plan_size(p, nullptr, st));
-    int dev = 0;
-    cudaGetDevice(&dev);
+    int dev = 0, cc[3] = {0, 0, p->h->sms};
+    TSG_CHECK(cudaGetDevice(&dev));
+    TSG_CHECK(cudaDeviceGetAttribute(&cc[0], cudaDevAttrComputeCapabilityMajor, dev));
+    TSG_CHECK(cudaDeviceGetAttribute(&cc[1], cudaDevAttrComputeCapabilityMinor, dev));
     uint64_t sig = 1469598103934665603ull;
-    sig = fnv(sig, &dev, sizeof(dev));
+    sig = fnv(sig, cc, sizeof(cc));
     sig = fnv(sig, &p->dtype, sizeof(p->dtype));
     for (int v : p->h->plan_hist) {
         // histogram shape on a log scale: tunes transfer between similar problems
@@ -1519,6 +1633,7 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_env_locked();
         auto it = g_tune_cache.find(sig);
         if (it != g_tune_cache.end()) {
             p->tune = it->second;
@@ -1585,12 +1700,59 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
     cudaEventDestroy(e1);
     if (rc != SPGEMM_OK) return rc;
     p->tune = best_t;
+    spgemm_status stored;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[sig] = best_t;
+        stored = store_tune_locked(sig, best_t);
     }
     if (chosen) *chosen = best_t;
-    return plan_size(p, nullptr, st);
+    TSG_TRY(plan_size(p, nullptr, st));
+    return stored;
+}
+
+spgemm_status spgemm_tune_cache_open(const char* path, int64_t* loaded) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_env_done = true;
+    const char* src = path ? path : std::getenv(kTuneEnv);
+    g_tune_path = src ? src : "";
+    long long n = g_tune_path.empty() ? 0 : load_tune_file_locked(g_tune_path);
+    if (loaded) *loaded = n < 0 ? 0 : n;
+    return n < 0 ? SPGEMM_ERR_INVALID_ARG : SPGEMM_OK;
+}
+
+spgemm_status spgemm_tune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+    g_tune_path.clear();
+    g_tune_env_done = true;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_tune_cache_store(uint64_t key, const spgemm_tune* t) {
+    if (!t) return SPGEMM_ERR_INVALID_ARG;
+    TSG_TRY(check_tune(t));
+    spgemm_tune x = *t;
+    x.validate = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return store_tune_locked(key, x);
+}
+
+spgemm_status spgemm_tune_cache_count(int64_t* n) {
+    if (!n) return SPGEMM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *n = (int64_t)g_tune_cache.size();
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_tune_cache_entry(int64_t index, uint64_t* key, spgemm_tune* t) {
+    if (!key || !t || index < 0) return SPGEMM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (index >= (int64_t)g_tune_cache.size()) return SPGEMM_ERR_INVALID_ARG;
+    auto it = g_tune_cache.begin();
+    std::advance(it, index);
+    *key = it->first;
+    *t = it->second;
+    return SPGEMM_OK;
 }
 
 spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count) {

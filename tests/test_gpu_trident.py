@@ -170,3 +170,46 @@ def test_plan_autotune_keeps_bits(tsg, handle):
     # every replay launches the same captured kernels
     assert n1 > n0 and plan.launch_count() - n1 == n1 - n0
     plan.close()
+
+
+def test_autotune_choice_persists_in_cache_file(tsg, tmp_path):
+    # the layout autotune chooses is appended to the cache file; a later
+    # process (here: the same one with its cache emptied) reads it back and
+    # reuses it without timing any candidate
+    shapes = gen.er_batch_shapes(8, seed=77, log2_lo=8, log2_hi=11)
+    pairs = [(gen.er(n, n, min(d, n), 3000 + 2 * t), gen.er(n, n, min(d, n), 3001 + 2 * t))
+             for t, (n, d) in enumerate(shapes)]
+    As = [tsg.DeviceCSR.from_host(a) for a, _ in pairs]
+    Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
+    f = tmp_path / "tune.txt"
+
+    def fields(t):
+        nb = t.num_bins
+        return nb, list(t.bin_upper)[:nb], list(t.bin_kernel)[:nb], t.warps_per_block, t.sym_warps_per_block
+
+    tsg.tune_cache_clear()
+    try:
+        assert tsg.tune_cache_open(str(f)) == 0
+        p1 = tsg.Plan(As, Bs)
+        before = p1.launch_count()
+        t1 = p1.autotune()
+        tuned = p1.launch_count() - before
+        lines = f.read_text().splitlines()
+        assert len(lines) == 1 and lines[0].startswith("tsg-tune-1 ")
+        p1.close()
+        tsg.tune_cache_clear()
+        assert tsg.tune_cache_open(str(f)) == 1
+        p2 = tsg.Plan(As, Bs)
+        before = p2.launch_count()
+        t2 = p2.autotune()
+        hit = p2.launch_count() - before
+        assert fields(t2) == fields(t1)
+        assert 0 < hit and 4 * hit < tuned
+        assert len(f.read_text().splitlines()) == 1  # a hit appends nothing
+        Cs = p2.execute()
+        torch.cuda.synchronize()
+        for (a, b), C in zip(pairs, Cs):
+            same(C, oracle.spgemm(a, b)[0])
+        p2.close()
+    finally:
+        tsg.tune_cache_clear()
