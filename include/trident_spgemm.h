@@ -257,6 +257,8 @@ spgemm_status spgemm_plan_execute(spgemm_plan* p, const spgemm_csr_out* C, int32
                                   spgemm_stream_t stream);
 spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spgemm_stream_t stream,
                                    spgemm_tune* chosen);
+spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count);
+spgemm_status spgemm_plan_destroy(spgemm_plan* p);
 
 /* Persistent autotune cache (host only).  The layouts spgemm_plan_autotune
  * chooses are kept per process, keyed by the GPU model (compute capability
@@ -287,8 +289,6 @@ spgemm_status spgemm_tune_cache_clear(void);
 spgemm_status spgemm_tune_cache_store(uint64_t key, const spgemm_tune* t);
 spgemm_status spgemm_tune_cache_count(int64_t* n);
 spgemm_status spgemm_tune_cache_entry(int64_t index, uint64_t* key, spgemm_tune* t);
-spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count);
-spgemm_status spgemm_plan_destroy(spgemm_plan* p);
 
 /* ------------------------------------------ trident partition (Sec. 3.2)
  *
