@@ -9,3 +9,4 @@ from .api import (BatchPlan, DeviceCSR, Handle, Plan, TridentPlan, batched, defa
                   fused_into, mcl_step, merge, numeric_into, permute, products, spgemm, spgemm_single_pass, symbolic,
                   tile_split, trident_bounds, trident_loads, trident_schedule, tune_cache_clear, tune_cache_entries,
                   tune_cache_open, tune_cache_store)
+from .autograd import Pattern, SpGEMMFunction, spgemm_values, transpose  # noqa: F401,E402

@@ -1,8 +1,9 @@
 """Differentiable SpGEMM on fixed sparsity patterns.
 
-``SpGEMMFunction.apply(a_val, b_val, A, B)`` returns the values of C = A B on
-C's pattern (computed once per pattern pair and cached on the ``Pattern``);
-its backward gives
+``SpGEMMFunction.apply(a_val, b_val, pat, deterministic)`` (or
+``spgemm_values``) returns the values of C = A B on C's pattern, which a
+``Pattern`` sizes once for the pattern pair (pat.A, pat.B); its backward
+gives
 
     dA_ik = sum_{j in B_k} G_ij b_kj    on pattern(A)
     dB_kj = sum_{i: k in A_i} a_ik G_ij on pattern(B)
