@@ -67,6 +67,10 @@ def workload(args):
     return n, A, B
 
 
+def workload_name(args) -> str:
+    return f"ER A*B n=2^{args.n_log2} d={args.d} f64 (seeds 0/1), plain product"
+
+
 def products(A, B) -> int:
     return int(np.diff(B.rowptr)[A.col].sum())
 
@@ -203,7 +207,7 @@ def run_reference(args):
     n, A, B = workload(args)
     import gen
     import oracle
-    rows = 1 << 15
+    rows = min(1 << 15, A.nrows)
     end = int(A.rowptr[rows])
     As = gen.CSR(rows, A.ncols, A.rowptr[:rows + 1].copy(), A.col[:end], A.val[:end])
     prods = products(As, B)
@@ -217,8 +221,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": round(val, 4), "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"ER A*B n=2^{args.n_log2} d={args.d} f64 (seeds 0/1)",
-                       "global_batch": 1, "seq_len": None, "parallelism": "replicas"},
+            "config": {"workload": workload_name(args), "parallelism": "single"},
             "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": f"first {rows} of {n} rows ({prods} products) per step"},
             "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -329,8 +332,7 @@ def run_native(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"ER A*B n=2^{args.n_log2} d={args.d} f64 (seeds 0/1), plain product",
-                           "model": None, "global_batch": world, "seq_len": None,
+                "config": {"workload": workload_name(args),
                            "parallelism": "replicas" if world > 1 else "single",
                            "products": prods, "nnz_c": nnz, "l2": "inputs+outputs > L2 (C = "
                            f"{nnz * 12 / 1e9:.2f} GB written per step)"},
