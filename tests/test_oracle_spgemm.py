@@ -141,6 +141,25 @@ def test_transpose_identity():
     assert np.array_equal(T.val, Ct.val)
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (7, 3), (50, 80), (0, 4)])
+def test_transpose_matches_dense(shape):
+    m, n = shape
+    X = gen.er_variable(m, n, min(n, 6), 15, np.float64, "normal", p_empty=0.2)
+    T = oracle.transpose(X)
+    assert (T.nrows, T.ncols) == (n, m)
+    assert np.array_equal(T.to_dense(), X.to_dense().T)
+    for i in range(n):
+        assert np.all(np.diff(T.col[T.rowptr[i]:T.rowptr[i + 1]]) > 0)
+
+
+def test_row_products_brute_force():
+    A = gen.er_variable(60, 40, 7, 16, np.float64, "uniform", p_empty=0.2)
+    B = gen.er_variable(40, 30, 9, 17, np.float64, "uniform", p_empty=0.2)
+    u = oracle.row_products(A, B)
+    blen = np.diff(B.rowptr)
+    assert u.tolist() == [int(sum(blen[k] for k in A.col[A.rowptr[i]:A.rowptr[i + 1]])) for i in range(A.nrows)]
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_scipy_cross_check(seed):
     # positive values: nothing cancels, so scipy keeps every structural entry
