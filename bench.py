@@ -15,10 +15,11 @@ algorithmic bytes per launch over its CUDA-event time, the measured peak,
 the DRAM traffic of the committed ncu capture while the kernel sources match
 it, and the per-product streaming model), the library's phase times, the
 oracle on the host cores (cpu_baseline), the same product end to end from
-pinned host memory (e2e), and, unless --no-extras, one line per further
-workload: the small ER case, the single-pass product, the trident grid, 256
-independent products, autograd, the restriction operator, the permuted
-banded matrix with its trident loads and volumes, and Markov clustering.
+pinned host memory (e2e), and, unless --no-extras, a "workloads" object with
+one entry per further workload: the small ER case, the single-pass product,
+the trident grid, 256 independent products, autograd, the restriction
+operator, the permuted banded matrix with its trident loads and volumes, and
+Markov clustering.  Rank 0 prints exactly one JSON line.
 
 Under torchrun (N > 1) every rank runs its own replica of the workload
 (independent problems, no collective on the data path); the time is the max
