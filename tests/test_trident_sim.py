@@ -89,6 +89,7 @@ def _run_grid(q, lam, case):
     (1, 2, (90, 70, 80, 9, 11)),      # two ranks: only the local allgather
     (2, 1, (101, 77, 93, 8, 21)),     # ragged tiles, point to point only
     (2, 2, (130, 96, 110, 10, 31)),   # eight ranks: both interconnects
+    (3, 1, (150, 121, 133, 9, 41)),   # nine ranks: sends and receives go round 3-cycles
 ])
 def test_alg1_message_flow_matches_oracle_and_volume_model(q, lam, case):
     import oracle
