@@ -43,8 +43,10 @@ def _worker(rank, world, port, q, lam, case, out):
     sys.path.insert(0, ROOT)
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
+    import datetime
+
     import torch.distributed as dist
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=90))
     try:
         import gen
         import oracle
@@ -75,12 +77,19 @@ def _run_grid(q, lam, case):
     for p in procs:
         p.start()
     got = dict()
-    for _ in procs:
-        rank, C, stats = out.get(timeout=150)
-        got[rank] = (C, stats)
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
+    try:
+        for _ in procs:
+            rank, C, stats = out.get(timeout=150)
+            got[rank] = (C, stats)
+        for p in procs:
+            p.join(timeout=60)
+            assert p.exitcode == 0
+    finally:
+        # a rank that failed leaves the others waiting in a collective: end them
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+                p.join(timeout=10)
     return got
 
 
