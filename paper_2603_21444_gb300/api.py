@@ -56,6 +56,27 @@ class DeviceCSR:
         return (self.row_ptr.cpu().numpy().astype(np.int64), self.col.cpu().numpy(),
                 None if self.val is None else self.val.cpu().numpy())
 
+    def save_npz(self, path) -> None:
+        """Write the matrix to a host .npz file (shape, row_ptr, col, val), e.g.
+        a Markov-clustering iterate between iterations."""
+        rp, col, val = self.to_host()
+        arrays = {"shape": np.array([self.nrows, self.ncols], dtype=np.int64), "row_ptr": rp, "col": col}
+        if val is not None:
+            arrays["val"] = val
+        np.savez(path, **arrays)
+
+    @staticmethod
+    def load_npz(path, device="cuda") -> "DeviceCSR":
+        """Read a matrix written by save_npz onto ``device``."""
+        with np.load(path) as f:
+            nrows, ncols = (int(x) for x in f["shape"])
+            rp = torch.from_numpy(f["row_ptr"].astype(np.int32))
+            col = torch.from_numpy(f["col"].astype(np.int32))
+            val = torch.from_numpy(f["val"].copy()) if "val" in f.files else None
+        if rp.numel() != nrows + 1 or int(rp[-1]) != col.numel() or (val is not None and val.numel() != col.numel()):
+            raise ValueError("inconsistent CSR arrays in " + str(path))
+        return DeviceCSR(nrows, ncols, rp.to(device), col.to(device), None if val is None else val.to(device))
+
     def as_in(self) -> CsrIn:
         return CsrIn(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
                      self.col.data_ptr() if self.nnz else None,
