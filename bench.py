@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--extras", dest="extras", action="store_true", default=True,
                    help="also time the trident grid, 256 products and the autograd workload")
     p.add_argument("--no-extras", dest="extras", action="store_false")
+    p.add_argument("--only", default=None,
+                   help="run one further workload alone (e.g. many_products, trident_grid) and print its entry")
+    p.add_argument("--many-count", type=int, default=256,
+                   help="products of the many_products workload (the first N of the 256; smaller for profiling)")
     return p.parse_args()
 
 
@@ -85,6 +89,20 @@ def algorithmic_bytes(A, B, nnz_c: int, val_bytes: int = 8):
                + 4 * (m + 1) + nnz_c * (4 + val_bytes))
     symbolic = 4 * (m + 1) + 4 * A.nnz + 4 * (k + 1) + 4 * B.nnz + 4 * (m + 1)
     return numeric, symbolic
+
+
+def csr_bytes(nrows: int, nnz: int, val_bytes: int = 8) -> int:
+    """Bytes of one CSR matrix: row_ptr (int32) + column indices + values."""
+    return 4 * (nrows + 1) + nnz * (4 + val_bytes)
+
+
+def workload_roofline(alg_bytes: int, ms: float, kernel: str, traffic=None) -> dict:
+    """Roofline of one workload's timed launch set: algorithmic (compulsory)
+    bytes over the measured time, against the measured HBM peak."""
+    peak, kind = peaks()
+    gbs = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": kernel, "algorithmic_bytes": int(alg_bytes), "achieved": round(gbs, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": kind, "traffic": traffic}
 
 
 class ClockSampler:
@@ -185,20 +203,68 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(A, B, budget_rows: int):
-    """The oracle, as it stands, on the first ``budget_rows`` rows of A."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _trials(fn, trials: int):
+    """One warm-up call, then `trials` timed calls: (mean s, min s)."""
+    fn()
+    ts = []
+    for _ in range(trials):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return float(np.mean(ts)), float(np.min(ts))
+
+
+def cpu_baseline(A, B, budget_rows: int, trials: int = 6):
+    """The oracle, as it stands, on the first ``budget_rows`` rows of A: one
+    warm-up and ``trials`` timed runs on all host cores, and the same with a
+    single thread on a quarter of those rows.  ``value`` is the all-core mean."""
     import gen
     import oracle
     rows = min(budget_rows, A.nrows)
-    end = int(A.rowptr[rows])
-    As = gen.CSR(rows, A.ncols, A.rowptr[:rows + 1].copy(), A.col[:end], A.val[:end])
+
+    def head(r):
+        end = int(A.rowptr[r])
+        return gen.CSR(r, A.ncols, A.rowptr[:r + 1].copy(), A.col[:end], A.val[:end])
+
+    As = head(rows)
     prods = products(As, B)
-    oracle.spgemm(As, B, with_scale=False)  # warm (first-touch, thread pool)
-    t0 = time.perf_counter()
-    oracle.spgemm(As, B, with_scale=False)
-    dt = time.perf_counter() - t0
-    return {"value": round(2 * prods / dt / 1e9, 4), "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"first {rows} of {A.nrows} rows ({prods} products), 1 timed run after 1 warm run"}
+    cores = oracle.get_threads()
+    mean_all, min_all = _trials(lambda: oracle.spgemm(As, B, with_scale=False), trials)
+    rows1 = max(1, rows // 4)
+    As1 = head(rows1)
+    prods1 = products(As1, B)
+    oracle.set_threads(1)
+    try:
+        mean_1, min_1 = _trials(lambda: oracle.spgemm(As1, B, with_scale=False), trials)
+    finally:
+        oracle.set_threads(cores)
+    g = lambda p, t: round(2 * p / t / 1e9, 4)
+    return {"value": g(prods, mean_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {rows} of {A.nrows} rows ({prods} products), 1 warm-up + {trials} timed runs",
+            "all_cores": {"mean": g(prods, mean_all), "best": g(prods, min_all), "threads": cores},
+            "single_thread": {"mean": g(prods1, mean_1), "best": g(prods1, min_1), "threads": 1,
+                              "sample": f"first {rows1} rows ({prods1} products)"},
+            "cpu_model": cpu_model()}
 
 
 def run_reference(args):
@@ -329,7 +395,7 @@ def run_native(args):
     if rank == 0:
         cb = None
         if not args.no_cpu_baseline and world == 1:
-            cb = cpu_baseline(A, B, 1 << 17)
+            cb = cpu_baseline(A, B, 1 << 18)
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -342,11 +408,9 @@ def run_native(args):
                 "single_pass": single, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if args.extras and world == 1:
             extras = {}
-            for name, fn in (("small_er", bench_small), ("trident_grid", bench_trident), ("many_products", bench_many),
-                             ("autograd", bench_autograd), ("restriction", bench_restriction),
-                             ("permutation", bench_permutation), ("markov_clustering", bench_mcl)):
+            for name in EXTRAS:
                 try:
-                    extras[name] = fn(tsg, 3)
+                    extras[name] = extra_fn(name)(tsg, 3)
                 except Exception as ex:  # report, keep the main line
                     extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
             line["workloads"] = extras
@@ -486,11 +550,21 @@ def bench_trident(tsg, steps):
     out["batched_graph_ms"] = round(t_replay, 3)
     out["batched_graph_gflops"] = round(2 * prods / t_replay / 1e6, 2)
     out["nnz_c"] = int(sum(fp.nnz))
+    # compulsory bytes of one replay: every A slice and B tile read once, the
+    # 64 output blocks (row_ptr, columns, values) written once
+    in_bytes = sum(csr_bytes(T.nrows, T.nnz) for row in plan.A_tiles + plan.B_tiles for T in row)
+    out_bytes = sum(csr_bytes(C.nrows, C.nnz) for C in fp.C)
+    out["roofline"] = workload_roofline(in_bytes + out_bytes, t_replay,
+                                        "fused plan replay (k_num_rows per bin, one CUDA graph)")
     # fused, fresh: sizing + numeric every step
     fresh = lambda: tsg.Plan(plan.As, plan.Bs, plan.group_ptr).execute(False)
     t_fresh = _time(fresh, max(1, steps // 4))
     out["batched_fresh_ms"] = round(t_fresh, 3)
     out["batched_fresh_gflops"] = round(2 * prods / t_fresh / 1e6, 2)
+    # fresh adds the sizing pass, which reads the index arrays once more
+    idx_bytes = sum(4 * (T.nrows + 1) + 4 * T.nnz for row in plan.A_tiles + plan.B_tiles for T in row)
+    out["roofline_fresh"] = workload_roofline(in_bytes + out_bytes + idx_bytes, t_fresh,
+                                              "fused plan, sized every call")
     del fp
     plan.fused = None
     torch.cuda.empty_cache()
@@ -510,25 +584,35 @@ def bench_trident(tsg, steps):
     return out
 
 
-def bench_many(tsg, steps):
+def bench_many(tsg, steps, count=256):
     """256 independent ER products, n log-uniform in [2^10, 2^16], 4..64 per
-    row, float64: one plan (one graph launch) against 256 product calls."""
+    row, float64: one plan (one graph launch) against 256 product calls.
+    count < 256 takes the first `count` products (profiling runs)."""
     import torch
     import gen
-    pairs = gen.er_batch(256)
+    pairs = gen.er_batch(256)[:count]
     prods = sum(products(a, b) for a, b in pairs)
     As = [tsg.DeviceCSR.from_host(a) for a, _ in pairs]
     Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
     h = tsg.Handle()
     plan = tsg.Plan(As, Bs)
     default_ms = _time(lambda: plan.execute(True), steps)
+    # compulsory bytes of one replay: each A_t, B_t read once, each C_t written once
+    alg = sum(csr_bytes(a.nrows, a.nnz) + csr_bytes(b.nrows, b.nnz) for a, b in zip(As, Bs))
+    alg += sum(csr_bytes(C.nrows, C.nnz) for C in plan.C)
+    nnz_c = int(sum(plan.nnz))
     tuned = plan.autotune()
     plan.execute(True)
     tuned_ms = _time(lambda: plan.execute(True), steps)
     fresh_ms = _time(lambda: tsg.Plan(As, Bs).execute(False), max(1, steps // 4))
     loop_ms = _time(lambda: [tsg.spgemm(a, b, h) for a, b in zip(As, Bs)], 1)
-    out = {"workload": "256 ER products, n=2^U(10,16), d=U{4..64}, f64", "products": prods,
+    best = min(default_ms, tuned_ms)
+    name = "256 ER products, n=2^U(10,16), d=U{4..64}, f64"
+    if count < 256:
+        name += f" (first {count})"
+    out = {"workload": name, "products": prods, "nnz_c": nnz_c,
            "batched_graph_ms": round(default_ms, 3), "batched_graph_autotuned_ms": round(tuned_ms, 3),
+           "roofline": workload_roofline(alg, best, "plan replay (k_num_rows per bin, one CUDA graph)"),
            "autotune": {"num_bins": tuned.num_bins, "bin_upper": list(tuned.bin_upper)[:tuned.num_bins],
                         "bin_kernel": list(tuned.bin_kernel)[:tuned.num_bins],
                         "warps_per_block": tuned.warps_per_block},
@@ -712,18 +796,53 @@ def bench_mcl(tsg, steps):
         t1.record()
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1)
+        # compulsory: the iterate read once (it is both factors), the kept
+        # entries written once; streaming: 8 B (column + value) per product
+        alg = csr_bytes(cur.nrows, int(rp[-1]), 4) + csr_bytes(cur.nrows, nxt.nnz, 4)
+        roof = workload_roofline(alg, ms, "k_mcl_rows (expansion fused with selection) + k_mcl_collect")
+        peak = roof["peak"]
+        roof["streaming_model"] = {"bytes": 8 * prods, "achieved_gbs": round(8 * prods / ms / 1e6, 1),
+                                   "frac": round(8 * prods / ms / 1e6 / peak, 4)}
         iters.append({"iteration": it + 1, "nnz_in": int(rp[-1]), "products": prods, "ms": round(ms, 3),
-                      "gflops": round(2 * prods / ms / 1e6, 2), "nnz_out": nxt.nnz})
+                      "gflops": round(2 * prods / ms / 1e6, 2), "nnz_out": nxt.nnz, "roofline": roof})
         cur = nxt
     h.close()
     return {"workload": "MCL on R-MAT scale 20 ef 16, f32 (f64 accumulation), 3 iterations", "iterations": iters,
             "total_ms": round(sum(x["ms"] for x in iters), 3)}
 
 
+EXTRAS = ("small_er", "trident_grid", "many_products", "autograd", "restriction", "permutation",
+          "markov_clustering")
+
+
+def extra_fn(name):
+    return {"small_er": bench_small, "trident_grid": bench_trident, "many_products": bench_many,
+            "autograd": bench_autograd, "restriction": bench_restriction, "permutation": bench_permutation,
+            "markov_clustering": bench_mcl}[name]
+
+
+def run_only(args):
+    """One further workload alone (profiling runs): builds the library, runs
+    it once and prints its entry as one JSON line."""
+    import torch
+
+    import __graft_entry__
+    if args.only not in EXTRAS:
+        raise SystemExit(f"--only: unknown workload {args.only!r}; one of {', '.join(EXTRAS)}")
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    __graft_entry__.build()
+    import paper_2603_21444_gb300 as tsg
+    fn = extra_fn(args.only)
+    res = fn(tsg, args.steps, args.many_count) if args.only == "many_products" else fn(tsg, args.steps)
+    print(json.dumps({"workload_only": args.only, args.only: res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_native(args)
 

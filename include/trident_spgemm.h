@@ -103,11 +103,19 @@ typedef struct {
  *   0: warp,  32   1: warp, 64    2: warp, 128    3: warp, 256    4: warp, 512
  *   5: 128 threads, 1024   6: 256 threads, 2048   7: 512 threads, 4096
  *   8: 512 threads, 8192   9: warp, 384   10: one thread per row, 16
- * The default bins are 16, 32, 64, 128, 256, 384, 512, ..., 8192 with
- * variants 10, 0, 1, 2, 3, 9, 4, 5, 6, 7, 8.  A variant whose capacity is
- * below bin_upper is rejected. */
+ *   11: 128 threads, 1024  12: 256 threads, 2048  13: 512 threads, 4096
+ *   14: 1024 threads, 8192   15: warp, 320
+ * Two accumulator kinds serve the block teams: variants 5-8 sort 64-bit
+ * (column, product) keys by bucket and rank inside each bucket; variants
+ * 11-14 keep the products in registers and run the warp teams' counting sort
+ * over the whole block (16-bit bucket counters, one bucket per column when
+ * the output has fewer columns than buckets, a dense accumulator).  Both
+ * add every output entry in the same order, so their results are identical.
+ * The default bins are 16, 32, 64, 128, 256, 320, 384, 512, ..., 8192 with
+ * variants 10, 0, 1, 2, 3, 15, 9, 4, 11, 12, 13, 14.  A variant whose
+ * capacity is below bin_upper is rejected. */
 #define SPGEMM_MAX_BINS 12
-#define SPGEMM_NUM_VARIANTS 11
+#define SPGEMM_NUM_VARIANTS 16
 enum { SPGEMM_ACC_SORT = 0 };
 
 typedef struct {
@@ -409,10 +417,9 @@ spgemm_status spgemm_mcl_collect(spgemm_handle* h, spgemm_csr_out* out, spgemm_s
  *
  * spgemm_csr_transpose_noalloc: the same result as spgemm_csr_transpose
  * (XT = X^T, rows sorted, arguments and layout identical) for callers that
- * must not allocate device memory: code running while a stream is captured
- * into a CUDA graph (cudaMalloc / cudaFree would break the capture), code
- * whose device memory is owned by an outside pool or budget, or paths that
- * cannot afford an allocation's implicit synchronisation.  It takes no
+ * must not allocate device memory: code whose device memory is owned by an
+ * outside pool or budget that forbids allocations behind its back, and paths
+ * that cannot afford an allocation's implicit synchronisation.  It takes no
  * handle and calls no allocating routine: its working memory is one fixed
  * array of SPGEMM_NOALLOC_SCRATCH_BYTES compiled into the library, held by
  * every GPU that loads it until the process exits.  A request whose working
@@ -420,9 +427,12 @@ spgemm_status spgemm_mcl_collect(spgemm_handle* h, spgemm_csr_out* out, spgemm_s
  * per nonzero, each part rounded up to 256 bytes) exceeds the array returns
  * SPGEMM_ERR_UNSUPPORTED without launching anything.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
- * calls share the array: calls whose GPU work overlaps (other streams,
- * unordered host threads) race.  Asynchronous on `stream`.
+ * device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset (or
+ * any other loss of the device's primary context) it is stale, so do not
+ * call this entry point again in that process.  All calls share the array:
+ * calls whose GPU work overlaps (other streams, unordered host threads)
+ * race.  Asynchronous on `stream`.
  * The paper has no counterpart: this entry point exists for callers of the
  * library, not for the method.
  */

@@ -67,14 +67,36 @@ class DeviceCSR:
 
     @staticmethod
     def load_npz(path, device="cuda") -> "DeviceCSR":
-        """Read a matrix written by save_npz onto ``device``."""
+        """Read a matrix written by save_npz onto ``device``.  The file is
+        checked on the host before anything reaches the device (kernels index
+        with these arrays): shape non-negative and within int32, row_ptr of
+        nrows + 1 non-decreasing entries from 0 to nnz < 2^31, every column
+        in [0, ncols), values (if any) one per entry.  Raises ValueError
+        otherwise."""
+        def bad(why):
+            return ValueError(f"invalid CSR file {path}: {why}")
+
         with np.load(path) as f:
-            nrows, ncols = (int(x) for x in f["shape"])
-            rp = torch.from_numpy(f["row_ptr"].astype(np.int32))
-            col = torch.from_numpy(f["col"].astype(np.int32))
-            val = torch.from_numpy(f["val"].copy()) if "val" in f.files else None
-        if rp.numel() != nrows + 1 or int(rp[-1]) != col.numel() or (val is not None and val.numel() != col.numel()):
-            raise ValueError("inconsistent CSR arrays in " + str(path))
+            shape = np.asarray(f["shape"])
+            rp64 = np.asarray(f["row_ptr"]).astype(np.int64)
+            col64 = np.asarray(f["col"]).astype(np.int64)
+            val = f["val"].copy() if "val" in f.files else None
+        if shape.shape != (2,) or shape.min() < 0 or shape.max() > 2**31 - 1:
+            raise bad("shape")
+        nrows, ncols = int(shape[0]), int(shape[1])
+        if rp64.ndim != 1 or rp64.size != nrows + 1:
+            raise bad("row_ptr length")
+        if rp64[0] != 0 or np.any(np.diff(rp64) < 0):
+            raise bad("row_ptr must start at 0 and not decrease")
+        if rp64[-1] != col64.size or col64.size > 2**31 - 1:
+            raise bad("row_ptr[-1] must equal the number of columns stored, below 2^31")
+        if col64.size and (col64.min() < 0 or col64.max() >= ncols):
+            raise bad("column index outside [0, ncols)")
+        if val is not None and val.size != col64.size:
+            raise bad("one value per entry")
+        rp = torch.from_numpy(rp64.astype(np.int32))
+        col = torch.from_numpy(col64.astype(np.int32))
+        val = None if val is None else torch.from_numpy(val)
         return DeviceCSR(nrows, ncols, rp.to(device), col.to(device), None if val is None else val.to(device))
 
     def as_in(self) -> CsrIn:

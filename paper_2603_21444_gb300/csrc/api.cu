@@ -157,10 +157,10 @@ spgemm_status grow_pinned(spgemm_handle* h, size_t bytes) {
 
 void default_tune(spgemm_tune* t) {
     std::memset(t, 0, sizeof(*t));
-    const int upper[11] = {16, 32, 64, 128, 256, 384, 512, 1024, 2048, 4096, 8192};
-    const int kernel[11] = {10, 0, 1, 2, 3, 9, 4, 5, 6, 7, 8};
-    t->num_bins = 11;
-    for (int b = 0; b < 11; ++b) {
+    const int upper[12] = {16, 32, 64, 128, 256, 320, 384, 512, 1024, 2048, 4096, 8192};
+    const int kernel[12] = {10, 0, 1, 2, 3, 15, 9, 4, 11, 12, 13, 14};
+    t->num_bins = 12;
+    for (int b = 0; b < 12; ++b) {
         t->bin_upper[b] = upper[b];
         t->bin_kernel[b] = kernel[b];
     }

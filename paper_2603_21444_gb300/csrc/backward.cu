@@ -167,6 +167,15 @@ __global__ void k_tr_scatter(const int* __restrict__ rp, const int* __restrict__
     }
 }
 
+// Rows of X^T up to kTrShort entries: one warp per row, each entry ranked by
+// a scan of its row (len^2 / 32 compares per lane).  Longer rows (a dense or
+// power-law column of X) go to k_tr_sort_long.
+constexpr int kTrShort = 1024;
+constexpr int kTrLongThreads = 1024;
+constexpr int kTrWindow = 1 << 19;          // keys per bitmap pass
+constexpr int kTrWords = kTrWindow / 32;    // 16384 words: 64 KB bitmap + 64 KB prefixes
+constexpr int kTrLongSmem = 2 * kTrWords * 4;
+
 // rows are sorted into tmp then copied back; keys within a row are distinct
 template <typename T>
 __global__ void k_tr_sort(const int* __restrict__ trp, int nrows_t, int* tcol, T* tval, int* tmpc, T* tmpv,
@@ -175,6 +184,7 @@ __global__ void k_tr_sort(const int* __restrict__ trp, int nrows_t, int* tcol, T
     const int warps = blockDim.x >> 5;
     for (int k = blockIdx.x * warps + (threadIdx.x >> 5); k < nrows_t; k += gridDim.x * warps) {
         const int lo = __ldg(trp + k), hi = __ldg(trp + k + 1);
+        if (hi - lo > kTrShort) continue;
         for (int e = lo + lane; e < hi; e += 32) {
             const int key = tcol[e];
             int rank = 0;
@@ -188,6 +198,76 @@ __global__ void k_tr_sort(const int* __restrict__ trp, int nrows_t, int* tcol, T
             if (has_val) tval[e] = tmpv[e];
         }
         __syncwarp();
+    }
+}
+
+// Long rows of X^T, one block each: the row's keys (distinct row indices of
+// X, in [0, nkeys)) are marked in a shared-memory bitmap over a window of
+// kTrWindow keys, the words' popcounts are scanned, and each entry's rank is
+// the keys below it -- earlier windows, earlier words, lower bits of its
+// word.  O(len + nkeys / 32) per window and row, for any row length.  Blocks
+// find the long rows by checking kTrLongThreads rows at a time.
+template <typename T>
+__global__ void __launch_bounds__(kTrLongThreads, 1)
+    k_tr_sort_long(const int* __restrict__ trp, int nrows_t, int nkeys, int* tcol, T* tval, int* tmpc, T* tmpv,
+                   bool has_val) {
+    extern __shared__ __align__(16) unsigned trsm[];
+    unsigned* bm = trsm;
+    unsigned* pre = trsm + kTrWords;
+    __shared__ int scratch[34];
+    __shared__ int longs[kTrLongThreads];
+    __shared__ int nlong;
+    const int tid = threadIdx.x;
+    for (long long k0 = (long long)blockIdx.x * kTrLongThreads; k0 < nrows_t;
+         k0 += (long long)gridDim.x * kTrLongThreads) {
+        if (tid == 0) nlong = 0;
+        __syncthreads();
+        const long long kk = k0 + tid;
+        if (kk < nrows_t && __ldg(trp + kk + 1) - __ldg(trp + kk) > kTrShort) longs[atomicAdd(&nlong, 1)] = (int)kk;
+        __syncthreads();
+        const int nl = nlong;
+        for (int x = 0; x < nl; ++x) {
+            const int k = longs[x];
+            const int lo = __ldg(trp + k), hi = __ldg(trp + k + 1);
+            int base = 0;  // keys in earlier windows
+            for (int w0 = 0; w0 < nkeys; w0 += kTrWindow) {
+                const int words = min(kTrWords, (nkeys - w0 + 31) / 32);
+                for (int i = tid; i < words; i += kTrLongThreads) bm[i] = 0u;
+                __syncthreads();
+                for (int e = lo + tid; e < hi; e += kTrLongThreads) {
+                    const unsigned r = (unsigned)(tcol[e] - w0);
+                    if (r < (unsigned)kTrWindow) atomicOr(bm + (r >> 5), 1u << (r & 31));
+                }
+                __syncthreads();
+                constexpr int per = kTrWords / kTrLongThreads;
+                const int beg = tid * per;
+                int loc = 0;
+                for (int i = beg; i < beg + per && i < words; ++i) loc += __popc(bm[i]);
+                int tot;
+                int run = Team<kTrLongThreads>::scan_excl(loc, &tot, scratch);
+                for (int i = beg; i < beg + per && i < words; ++i) {
+                    pre[i] = (unsigned)run;
+                    run += __popc(bm[i]);
+                }
+                __syncthreads();
+                for (int e = lo + tid; e < hi; e += kTrLongThreads) {
+                    const int key = tcol[e];
+                    const unsigned r = (unsigned)(key - w0);
+                    if (r < (unsigned)kTrWindow) {
+                        const int rank = base + (int)pre[r >> 5] + __popc(bm[r >> 5] & ((1u << (r & 31)) - 1u));
+                        tmpc[lo + rank] = key;
+                        if (has_val) tmpv[lo + rank] = tval[e];
+                    }
+                }
+                base += tot;
+                __syncthreads();
+            }
+            for (int e = lo + tid; e < hi; e += kTrLongThreads) {
+                tcol[e] = tmpc[e];
+                if (has_val) tval[e] = tmpv[e];
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -223,6 +303,21 @@ cudaError_t launch_transpose(int dtype, const int* rp, const int* col, const voi
         else
             k_tr_sort<float><<<blocks, 256, 0, s>>>(trp, ncols, tcol, static_cast<float*>(tval), tmpc,
                                                     static_cast<float*>(tmpv), val != nullptr);
+        // rows longer than kTrShort exist only if nnz exceeds it
+        if (nnz > kTrShort) {
+            const int lb = (int)std::min<long long>(((long long)ncols + kTrLongThreads - 1) / kTrLongThreads, sms);
+            if (dtype == 1) {
+                cudaFuncSetAttribute(k_tr_sort_long<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrLongSmem);
+                k_tr_sort_long<double><<<lb, kTrLongThreads, kTrLongSmem, s>>>(
+                    trp, ncols, nrows, tcol, static_cast<double*>(tval), tmpc, static_cast<double*>(tmpv),
+                    val != nullptr);
+            } else {
+                cudaFuncSetAttribute(k_tr_sort_long<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrLongSmem);
+                k_tr_sort_long<float><<<lb, kTrLongThreads, kTrLongSmem, s>>>(
+                    trp, ncols, nrows, tcol, static_cast<float*>(tval), tmpc, static_cast<float*>(tmpv),
+                    val != nullptr);
+            }
+        }
     }
     return cudaGetLastError();
 }

@@ -40,13 +40,24 @@ struct GroupDev {
 
 // kernel variants: team size and capacity (products per team); variant 9,
 // a warp holding 384, sits between 3 and 4, and variant 10, one thread per
-// row holding 16, below 0 (appended to keep indices stable)
-constexpr int kNumVariants = 11;
+// row holding 16, below 0 (appended to keep indices stable).  Variants 5-8
+// are block teams with the rank-in-bucket accumulator (rows.cuh), variants
+// 11-14 block teams of 4, 8, 16, 32 warps running the warp counting sort
+// across the block (rows_team.cuh): a second accumulator kind for the same
+// capacities, 1024 to 8192.  Variant 15, a warp holding 320 (10 per lane),
+// sits between 3 and 9: rows just above 256 products (the trident grid's
+// rows scatter around 256) without the 384 variant's register and shared
+// memory cost.
+constexpr int kNumVariants = 16;
+__host__ __device__ constexpr bool variant_is_team(int v) { return v >= 11 && v <= 14; }
 __host__ __device__ constexpr int variant_team(int v) {
-    return v == 10 ? 1 : ((v <= 4 || v == 9) ? 32 : (v == 5 ? 128 : (v == 6 ? 256 : 512)));
+    return variant_is_team(v) ? (128 << (v - 11))
+                              : (v == 10 ? 1 : ((v <= 4 || v == 9 || v == 15) ? 32
+                                                                             : (v == 5 ? 128 : (v == 6 ? 256 : 512))));
 }
 __host__ __device__ constexpr int variant_per(int v) {
-    return v == 10 ? 16 : (v <= 4 ? (1 << v) : (v == 9 ? 12 : (v == 8 ? 16 : 8)));
+    return variant_is_team(v) ? 8
+                              : (v == 15 ? 10 : (v == 10 ? 16 : (v <= 4 ? (1 << v) : (v == 9 ? 12 : (v == 8 ? 16 : 8)))));
 }
 constexpr int kThreadRows = 256;  // rows (threads) per block of the thread-per-row variant
 // largest power of two <= x (x >= 1)

@@ -1,20 +1,21 @@
 // An allocation-free variant of the CSR transpose for callers that may not
 // allocate device memory.
 //
-// Who needs it: code that runs while a stream is being captured into a CUDA
-// graph (cudaMalloc / cudaFree are not stream operations and break a
-// capture), code whose device memory is owned by an outside pool or budget
-// that forbids allocations behind its back, and latency-critical paths where
-// an allocation's implicit device synchronisation is not acceptable.  Such a
-// caller passes inputs and outputs it allocated itself; all working memory
-// comes from one fixed array compiled into this library.
+// Who needs it: code whose device memory is owned by an outside pool or
+// budget that forbids allocations behind its back, and latency-critical
+// paths where an allocation's implicit device synchronisation is not
+// acceptable.  Such a caller passes inputs and outputs it allocated itself;
+// all working memory comes from one fixed array compiled into this library.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kNoAllocScratchBytes) until the process exits.  In host
 // code the variable's name is only a host-side stand-in, never a device
 // address, so its address is obtained with cudaGetSymbolAddress, once per
 // device, with that device current, by the first call on that device.  That
-// first call must therefore come before any stream capture begins.
+// first call must therefore come before any stream capture begins.  The
+// address is cached for the life of the process; a device reset
+// (cudaDeviceReset) invalidates it, and the entry point must not be called
+// again afterwards.
 //
 // Every call uses the same array and leaves its contents behind; the parts
 // that must start at zero (column counts and cursors) are cleared on the

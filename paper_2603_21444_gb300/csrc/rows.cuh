@@ -202,9 +202,14 @@ __device__ __forceinline__ void sym_row(const RowArgs& a, int unit, char* sm) {
 // otherwise element by element.  Product slot e of the lane holds product
 // p = 4 (32 (e / 4) + L) + e % 4.
 
+// When PER is not a multiple of 4 (the 320-product variant, PER = 10) the
+// last PER % 4 slots form a narrower tail chunk after the 4-wide ones: lane L
+// takes products 128 (PER / 4) + R L + v, v < R = PER % 4.
 template <int PER>
 __device__ __forceinline__ int chunk_product(int lane, int e) {
     constexpr int W = PER < 4 ? PER : 4;
+    constexpr int NC = PER / W, R = PER - NC * W;
+    if (R > 0 && e >= NC * W) return 32 * W * NC + R * lane + (e - NC * W);
     return W * (32 * (e / W) + lane) + e % W;
 }
 
@@ -245,15 +250,42 @@ __device__ __forceinline__ int owner_of(const int* m_pre, int nA, int p) {
 }
 
 // col[e] = column of the lane's e-th product (-1 past u); with VALS,
-// val[e] = a_ik * b_kj (merge: b_kj) and ins[e] = its instance.
+// val[e] = a_ik * b_kj (merge: b_kj) and ins[e] = its instance.  The warp
+// covers products [pbase, pbase + 32 PER) of the row (pbase = 0 for a warp
+// team; warp w of a block team takes pbase = 32 PER w).
 template <int PER, bool VALS, typename T>
 __device__ __forceinline__ void gather_chunks(const RowArgs& a, int ib, int nA, int u, const int* m_pre,
                                               const int* m_bs, const T* m_a, const unsigned char* m_inst, int lane,
-                                              int (&col)[PER], T (&val)[PER], int (&ins)[PER]) {
+                                              int (&col)[PER], T (&val)[PER], int (&ins)[PER], int pbase = 0) {
     constexpr int W = PER < 4 ? PER : 4;  // chunk width
+    constexpr int NC = PER / W, R = PER - NC * W;
+    if constexpr (R > 0) {
+        // tail chunk (PER % 4 products per lane), element by element
+        const int pt = pbase + 32 * W * NC + R * lane;
 #pragma unroll
-    for (int c = 0; c < PER / W; ++c) {
-        const int p0 = W * (32 * c + lane);
+        for (int v = 0; v < R; ++v) {
+            const int e = NC * W + v;
+            col[e] = -1;
+            if (VALS) val[e] = T(0);
+            ins[e] = 0;
+            const int p = pt + v;
+            if (p < u) {
+                const int t = owner_of(m_pre, nA, p);
+                const int ti = m_inst[t];
+                const InstDev* I = a.inst + ib + ti;
+                const int f = m_bs[t] + (p - m_pre[t]);
+                col[e] = __ldg(I->bcol + f);
+                if (VALS) {
+                    const T bv = __ldg(reinterpret_cast<const T*>(I->bval) + f);
+                    val[e] = a.merge ? bv : mul_rn(m_a[t], bv);
+                }
+                ins[e] = ti;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int p0 = pbase + W * (32 * c + lane);
 #pragma unroll
         for (int v = 0; v < W; ++v) {
             col[W * c + v] = -1;
@@ -1677,7 +1709,8 @@ __device__ __forceinline__ void num_row_warp(const RowArgs& a, int unit, char* s
 
 template <int TEAM, int PER, typename T>
 __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : (PER == 12 ? 256 : 512)) : TEAM,
-                                    TEAM == 32 && PER == 12 ? 3 : 1) k_num_rows(RowArgs a) {
+                                    TEAM == 32 && PER == 12 ? 3 : (TEAM == 32 && PER == 10 ? 2 : 1))
+    k_num_rows(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     constexpr int CAP = TEAM * PER;
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
@@ -1715,7 +1748,7 @@ __global__ void __launch_bounds__(TEAM == 32 ? (PER <= 8 ? 1024 : (PER == 12 ? 2
 }
 
 template <int PER, typename T>
-__global__ void __launch_bounds__(PER <= 8 ? 1024 : (PER == 12 ? 256 : 512), PER == 12 ? 3 : 1)
+__global__ void __launch_bounds__(PER <= 8 ? 1024 : (PER == 12 ? 256 : 512), PER == 12 ? 3 : (PER == 10 ? 2 : 1))
     k_num_fused(RowArgs a, FusedCtl fc) {
     extern __shared__ __align__(16) char smem[];
     __shared__ long long sh_off[32];

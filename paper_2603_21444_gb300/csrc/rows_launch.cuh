@@ -3,6 +3,7 @@
 
 #include "internal.h"
 #include "rows.cuh"
+#include "rows_team.cuh"
 
 namespace tsg {
 
@@ -29,6 +30,7 @@ struct VariantShape {
     static constexpr int TEAM = variant_team(V);
     static constexpr int PER = variant_per(V);
     static constexpr int CAP = TEAM * PER;
+    static constexpr bool TEAMK = variant_is_team(V);  // block team running the warp counting sort
 };
 
 // Calls f(std::integral_constant-like tag) for the runtime variant v.
@@ -46,6 +48,11 @@ inline cudaError_t dispatch_variant(int v, F&& f) {
         case 8: return f(VariantShape<8>());
         case 9: return f(VariantShape<9>());
         case 10: return f(VariantShape<10>());
+        case 11: return f(VariantShape<11>());
+        case 12: return f(VariantShape<12>());
+        case 13: return f(VariantShape<13>());
+        case 14: return f(VariantShape<14>());
+        case 15: return f(VariantShape<15>());
         default: return cudaErrorInvalidValue;
     }
 }

@@ -48,8 +48,9 @@ def test_host_only_calls(lib):
     assert b"sm_103a" in lib.spgemm_version()
     t = _abi.Tune()
     assert lib.spgemm_default_tune(ctypes.byref(t)) == 0
-    assert t.num_bins == 11 and list(t.bin_upper)[:11] == [16, 32, 64, 128, 256, 384, 512, 1024, 2048, 4096, 8192]
-    assert list(t.bin_kernel)[:11] == [10, 0, 1, 2, 3, 9, 4, 5, 6, 7, 8]
+    assert t.num_bins == 12
+    assert list(t.bin_upper)[:12] == [16, 32, 64, 128, 256, 320, 384, 512, 1024, 2048, 4096, 8192]
+    assert list(t.bin_kernel)[:12] == [10, 0, 1, 2, 3, 15, 9, 4, 11, 12, 13, 14]
     assert t.warps_per_block == 16 and t.sym_warps_per_block == 8
     assert lib.spgemm_default_tune(None) == 1
     assert lib.spgemm_destroy(None) == 0

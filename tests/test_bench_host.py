@@ -63,3 +63,22 @@ def test_other_ranks_of_the_reference_arm_exit_quietly():
                           "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env, timeout=300,
                          cwd=ROOT)
     assert out.returncode == 0 and not [x for x in out.stdout.splitlines() if x.startswith("{")]
+
+
+def test_cpu_baseline_reports_trials_threads_and_model():
+    import bench
+    A = gen.er(2048, 2048, 8, 0)
+    cb = bench.cpu_baseline(A, A, 512, trials=2)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
+    assert cb["all_cores"]["threads"] == cb["cores"] and cb["single_thread"]["threads"] == 1
+    assert cb["all_cores"]["best"] >= cb["all_cores"]["mean"] > 0
+    assert isinstance(cb["cpu_model"], str) and cb["cpu_model"]
+    assert oracle.get_threads() == cb["cores"]  # the thread count is restored
+
+
+def test_workload_roofline_arithmetic():
+    import bench
+    r = bench.workload_roofline(6_000_000_000, 2.0, "k")
+    assert r["achieved"] == 3000.0 and r["unit"] == "GB/s" and r["bound"] == "hbm"
+    assert abs(r["frac"] - 3000.0 / r["peak"]) < 1e-4
+    assert bench.csr_bytes(3, 5, 8) == 16 + 60 and bench.csr_bytes(3, 5, 4) == 16 + 40

@@ -73,6 +73,34 @@ def test_transpose_matches_oracle(tsg, handle, dtype):
     assert np.array_equal(rp, ref.rowptr) and np.array_equal(col, ref.col) and np.array_equal(val, ref.val)
 
 
+def long_column_matrix(nrows, ncols, lens, seed, dtype):
+    """X with 2 random entries per row in columns >= 100 plus columns
+    j < 100 holding exactly lens[j] entries at distinct random rows: rows of
+    X^T far longer than one warp's share."""
+    rng = np.random.default_rng(seed)
+    r = [np.repeat(np.arange(nrows), 2)]
+    c = [rng.integers(100, ncols, 2 * nrows)]
+    for j, L in lens.items():
+        r.append(rng.choice(nrows, size=L, replace=False))
+        c.append(np.full(L, j))
+    rows, cols = np.concatenate(r), np.concatenate(c)
+    key = np.unique(rows.astype(np.int64) * ncols + cols)
+    return gen.from_coo(nrows, ncols, key // ncols, key % ncols, rng.normal(size=key.size).astype(dtype))
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_transpose_long_columns(tsg, handle, dtype):
+    # columns of 1024 (the warp path's limit), 1025, 20000 and 300000
+    # entries; 700000 rows of X: two bitmap windows of row indices
+    from paper_2603_21444_gb300 import autograd as ag
+    X = long_column_matrix(700000, 5000, {3: 20000, 7: 1025, 11: 1024, 40: 300000}, 5, dtype)
+    T = ag.transpose(tsg.DeviceCSR.from_host(X), handle)
+    torch.cuda.synchronize()
+    ref = oracle.transpose(X)
+    rp, col, val = T.to_host()
+    assert np.array_equal(rp, ref.rowptr) and np.array_equal(col, ref.col) and np.array_equal(val, ref.val)
+
+
 def test_autograd_gradcheck_tiny(tsg, handle):
     from paper_2603_21444_gb300 import autograd as ag
     A = gen.er_variable(12, 9, 4, 1, np.float64, "normal")

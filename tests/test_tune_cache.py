@@ -42,7 +42,7 @@ def test_store_then_reload(tsg, tmp_path):
     tsg.tune_cache_store(0xFEDCBA9876543210, b)
     lines = f.read_text().splitlines()
     assert len(lines) == 2
-    assert lines[0].startswith("tsg-tune-1 0000000000001234 11 8 8 16 10 32 0 64 1")
+    assert lines[0].startswith("tsg-tune-1 0000000000001234 12 8 8 16 10 32 0 64 1")
     assert lines[1] == "tsg-tune-1 fedcba9876543210 4 32 8 128 2 512 4 2048 6 8192 8"
     tsg.tune_cache_clear()
     assert tsg.tune_cache_entries() == []

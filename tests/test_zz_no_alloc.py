@@ -1,6 +1,7 @@
 """The allocation-free transpose (for callers that may not allocate device
-memory, e.g. while a stream is being captured into a CUDA graph, or under an
-outside memory pool) against the allocating entry point.
+memory: code under an outside memory pool or budget, or paths that cannot
+take an allocation's implicit synchronisation) against the allocating entry
+point.
 
 This file is collected last so that, if it fails, a run stopping at the first
 failure has already run every other test; it also passes alone in a fresh
@@ -54,6 +55,25 @@ def test_noalloc_matches_allocating_transpose_twice(lib, dtype):
         # a transpose moves values without arithmetic: equal bit for bit
         for a, b in zip(T.to_host(), R.to_host()):
             assert np.array_equal(a, b)
+
+
+def test_noalloc_long_columns_match_allocating_transpose(lib):
+    import paper_2603_21444_gb300 as tsg
+    from paper_2603_21444_gb300 import autograd as ag
+    # columns of 1025 and 30000 entries (rows of X^T longer than one warp
+    # sorts) next to short ones, 600000 rows of X (two windows of row indices)
+    rng = np.random.default_rng(3)
+    n, nc = 600000, 2000
+    rows = [np.arange(n), rng.choice(n, 1025, replace=False), rng.choice(n, 30000, replace=False)]
+    cols = [rng.integers(10, nc, n), np.full(1025, 1), np.full(30000, 5)]
+    key = np.unique(np.concatenate(rows).astype(np.int64) * nc + np.concatenate(cols))
+    X = tsg.DeviceCSR.from_host(gen.from_coo(n, nc, key // nc, key % nc, rng.normal(size=key.size)))
+    rc, T = _noalloc_transpose(lib, X, torch.float64)
+    assert rc == 0
+    R = ag.transpose(X)
+    torch.cuda.synchronize()
+    for a, b in zip(T.to_host(), R.to_host()):
+        assert np.array_equal(a, b)
 
 
 def test_noalloc_rejects_oversize_request(lib):
