@@ -544,6 +544,11 @@ def bench_trident(tsg, steps):
            "products": prods, "partition_ms": round(t_split, 3)}
     # fused, persistent: sized once, numeric replayed from a CUDA graph
     fp = plan.fused_plan()
+    # bins one after another, then concurrent (the default)
+    fp.set_concurrent_bins(False)
+    fp.execute(True)
+    out["batched_graph_sequential_bins_ms"] = round(_time(lambda: fp.execute(True), steps), 3)
+    fp.set_concurrent_bins(True)
     fp.execute(True)
     torch.cuda.synchronize()
     t_replay = _time(lambda: fp.execute(True), steps)
@@ -596,6 +601,9 @@ def bench_many(tsg, steps, count=256):
     Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
     h = tsg.Handle()
     plan = tsg.Plan(As, Bs)
+    plan.set_concurrent_bins(False)
+    sequential_ms = _time(lambda: plan.execute(True), steps)
+    plan.set_concurrent_bins(True)
     default_ms = _time(lambda: plan.execute(True), steps)
     # compulsory bytes of one replay: each A_t, B_t read once, each C_t written once
     alg = sum(csr_bytes(a.nrows, a.nnz) + csr_bytes(b.nrows, b.nnz) for a, b in zip(As, Bs))
@@ -612,6 +620,7 @@ def bench_many(tsg, steps, count=256):
         name += f" (first {count})"
     out = {"workload": name, "products": prods, "nnz_c": nnz_c,
            "batched_graph_ms": round(default_ms, 3), "batched_graph_autotuned_ms": round(tuned_ms, 3),
+           "batched_graph_sequential_bins_ms": round(sequential_ms, 3),
            "roofline": workload_roofline(alg, best, "plan replay (k_num_rows per bin, one CUDA graph)"),
            "autotune": {"num_bins": tuned.num_bins, "bin_upper": list(tuned.bin_upper)[:tuned.num_bins],
                         "bin_kernel": list(tuned.bin_kernel)[:tuned.num_bins],

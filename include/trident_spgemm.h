@@ -268,6 +268,17 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
 spgemm_status spgemm_plan_launch_count(const spgemm_plan* p, int64_t* count);
 spgemm_status spgemm_plan_destroy(spgemm_plan* p);
 
+/* Concurrent bins (Sec. 3.3's asynchronous C-stationary tiles: no global
+ * barrier between independent pieces of work).  The rows of different bins
+ * are disjoint, so by default every call forks its per-bin launches onto
+ * private streams of the handle (each first waits for the work already on
+ * the call's stream) and joins them back before anything that needs all
+ * bins; in a plan's CUDA graph they are parallel nodes.  enable = 0 issues
+ * them one after another on the call's stream instead (the same results).
+ * The plan variant drops the plan's captured graph. */
+spgemm_status spgemm_set_concurrent_bins(spgemm_handle* h, int32_t enable);
+spgemm_status spgemm_plan_set_concurrent_bins(spgemm_plan* p, int32_t enable);
+
 /* Persistent autotune cache (host only).  The layouts spgemm_plan_autotune
  * chooses are kept per process, keyed by the GPU model (compute capability
  * and SM count), the dtype and the shape of the product-count histogram
@@ -319,6 +330,19 @@ spgemm_status spgemm_tune_cache_entry(int64_t index, uint64_t* key, spgemm_tune*
 spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* X, int32_t nrp,
                                 const int32_t* row_bounds, int32_t ncp, const int32_t* col_bounds,
                                 spgemm_csr_out* tiles, int64_t* tile_nnz, spgemm_stream_t stream);
+
+/* spgemm_trident_bounds: the boundaries of the trident split of [0, n)
+ * (Sec. 3.2) for a grid q x q x lambda: coarse tile t is [coarse[t],
+ * coarse[t+1]) with coarse[t] = floor(t n / q), t = 0..q; each coarse tile
+ * [lo, hi) is cut into lambda contiguous slices, slice s of tile t starting
+ * at fine[t lambda + s] = lo + floor(s (hi - lo) / lambda), and
+ * fine[q lambda] = n.  Host arrays of q + 1 (coarse) and q lambda + 1 (fine)
+ * entries; either may be NULL.  n >= 0, q >= 1, lambda >= 1 (products
+ * computed in 64 bits); otherwise SPGEMM_ERR_INVALID_ARG.  Host-only: needs
+ * no handle and no device.  These are the row bounds (fine) and column
+ * bounds (coarse) spgemm_tile_split takes for A, and the coarse bounds on
+ * both sides for B. */
+spgemm_status spgemm_trident_bounds(int32_t n, int32_t q, int32_t lambda, int32_t* coarse, int32_t* fine);
 
 /* ------------------------------------ static-Cannon rounds (Alg. 1, Eq. 2)
  *

@@ -76,6 +76,7 @@ SIGNATURES = {
                         ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, ctypes.POINTER(Tune), P], ctypes.c_int),
     "spgemm_tile_split": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), I32, ctypes.POINTER(I32), I32,
                            ctypes.POINTER(I32), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),
+    "spgemm_trident_bounds": ([I32, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
     "spgemm_trident_schedule": ([I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
                                 ctypes.c_int),
     "spgemm_backward": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, P,
@@ -87,6 +88,8 @@ SIGNATURES = {
     "spgemm_plan_execute": ([P, ctypes.POINTER(CsrOut), I32, P], ctypes.c_int),
     "spgemm_plan_autotune": ([P, ctypes.POINTER(CsrOut), P, ctypes.POINTER(Tune)], ctypes.c_int),
     "spgemm_plan_launch_count": ([P, I64P], ctypes.c_int),
+    "spgemm_set_concurrent_bins": ([P, I32], ctypes.c_int),
+    "spgemm_plan_set_concurrent_bins": ([P, I32], ctypes.c_int),
     "spgemm_tune_cache_open": ([ctypes.c_char_p, I64P], ctypes.c_int),
     "spgemm_tune_cache_clear": ([], ctypes.c_int),
     "spgemm_tune_cache_store": ([ctypes.c_uint64, ctypes.POINTER(Tune)], ctypes.c_int),

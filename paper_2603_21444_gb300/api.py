@@ -168,6 +168,10 @@ class Handle:
     def set_timing(self, on: bool):
         check(_abi.lib().spgemm_set_timing(self._h, 1 if on else 0), "spgemm_set_timing")
 
+    def set_concurrent_bins(self, enable: bool):
+        """Per-bin launches as parallel branches (default) or one after another."""
+        check(_abi.lib().spgemm_set_concurrent_bins(self._h, 1 if enable else 0), "spgemm_set_concurrent_bins")
+
     def set_workspace_limit(self, nbytes: int | None):
         """Cap the device bytes this handle's workspace may hold (None: no
         cap); a call that would grow past it raises SPGEMM_ERR_OOM."""
@@ -367,11 +371,12 @@ def batched(As, Bs, group_ptr=None, handle: Handle | None = None, tune: Tune | N
 
 def trident_bounds(n: int, q: int, lam: int = 1):
     """(coarse, fine) boundaries of the hybrid 2D + 1D split of [0, n) (paper
-    Sec. 3.2): coarse tile t is [floor(t n / q), floor((t+1) n / q)); each is
-    cut into lam contiguous slices lo + floor(s (hi - lo) / lam)."""
-    coarse = [(t * n) // q for t in range(q + 1)]
-    fine = [coarse[t] + (s * (coarse[t + 1] - coarse[t])) // lam for t in range(q) for s in range(lam)] + [n]
-    return coarse, fine
+    Sec. 3.2) from the library (``spgemm_trident_bounds``): coarse tile t
+    starts at floor(t n / q), each cut into lam contiguous slices."""
+    coarse = (ctypes.c_int32 * (q + 1))()
+    fine = (ctypes.c_int32 * (q * lam + 1))()
+    check(_abi.lib().spgemm_trident_bounds(n, q, lam, coarse, fine), "spgemm_trident_bounds")
+    return list(coarse), list(fine)
 
 
 def tile_split(X: DeviceCSR, row_bounds, col_bounds, handle: Handle | None = None, stream=None):
@@ -547,6 +552,11 @@ class Plan:
         c = ctypes.c_int64()
         check(_abi.lib().spgemm_plan_launch_count(self._p, ctypes.byref(c)), "spgemm_plan_launch_count")
         return int(c.value)
+
+    def set_concurrent_bins(self, enable: bool):
+        """Per-bin launches as parallel branches (default) or one after another."""
+        check(_abi.lib().spgemm_plan_set_concurrent_bins(self._p, 1 if enable else 0),
+              "spgemm_plan_set_concurrent_bins")
 
     def close(self):
         if self._p:

@@ -78,6 +78,7 @@ struct spgemm_handle {
     long long ws_limit = -1;              // cap on the device bytes held by the buffers above (-1: none)
     int wait_limit = kLookbackSpinLimit;  // polls of a look-back wait of the single-pass product
     int hold_tile = -1;                   // fault injection: a look-back entry never published
+    int only_bin = -1;                    // autotuner: a fill call launches this bin's kernel alone
     std::vector<PhaseEvent> pending;
     std::vector<cudaEvent_t> spare;
     cudaStream_t last_stream = nullptr;
@@ -85,6 +86,13 @@ struct spgemm_handle {
     int occ_sym[kNumVariants];
     int occ_num[2][kNumVariants];
     std::vector<cudaStream_t> streams_used;
+    // branches for the per-bin launches of one call: bins hold disjoint rows,
+    // so their kernels run concurrently (forked from the call's stream,
+    // joined back before anything that needs every bin)
+    bool concurrent_bins = true;
+    cudaStream_t side[kMaxBins + 1] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxBins + 1] = {};
     // the last descriptor block copied to the device (identical blocks are
     // not copied again, so a repeated fill call launches kernels only)
     std::vector<char> last_stage;
@@ -267,6 +275,48 @@ void note_stream(spgemm_handle* h, cudaStream_t s) {
     if (std::find(h->streams_used.begin(), h->streams_used.end(), s) == h->streams_used.end())
         h->streams_used.push_back(s);
 }
+
+// Fork / join of the per-bin launches.  next() hands out a branch stream
+// that first waits for everything issued on st so far; join() makes st wait
+// for every branch handed out.  With concurrency off every branch is st.
+// Under stream capture the branches become parallel graph nodes.
+struct BinFork {
+    spgemm_handle* h;
+    cudaStream_t st;
+    bool on;
+    int used = 0;
+    cudaError_t err = cudaSuccess;
+    BinFork(spgemm_handle* h_, cudaStream_t st_) : h(h_), st(st_), on(h_->concurrent_bins) {
+        if (!on) return;
+        if (!h->fork_ev) err = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventRecord(h->fork_ev, st);
+        if (err != cudaSuccess) on = false;
+    }
+    cudaStream_t next() {
+        if (!on || used > kMaxBins) return st;
+        const int i = used;
+        if (!h->side[i]) {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                err = e;
+                return st;
+            }
+        }
+        if (cudaStreamWaitEvent(h->side[i], h->fork_ev, 0) != cudaSuccess) return st;
+        ++used;
+        return h->side[i];
+    }
+    cudaError_t join() {
+        for (int i = 0; i < used; ++i) {
+            cudaError_t e = cudaEventRecord(h->join_ev[i], h->side[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->join_ev[i], 0);
+            if (e != cudaSuccess) return e;
+        }
+        used = 0;
+        return err;
+    }
+};
 
 struct Validate {
     const int* rp;
@@ -515,18 +565,17 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     if (sizing) {
         {
             PhaseScope ps(h, 1, st);
+            BinFork fork(h, st);
             for (int b = 0; b < nb; ++b) {
                 const int v = tune.bin_kernel[b];
                 la.bin = b;
-                TSG_CHECK(launch_sym_rows(v, la, h->sms * h->occ_sym[v], sym_wpb(v, swpb), st));
+                TSG_CHECK(launch_sym_rows(v, la, h->sms * h->occ_sym[v], sym_wpb(v, swpb), fork.next()));
                 ++h->launches;
             }
-        }
-        {
-            PhaseScope ps(h, 4, st);
             la.bin = nb;
-            TSG_CHECK(launch_sym_heavy(la, h->sms, chunk, st));
+            TSG_CHECK(launch_sym_heavy(la, h->sms, chunk, fork.next()));
             ++h->launches;
+            TSG_CHECK(fork.join());
         }
         {
             PhaseScope ps(h, 2, st);
@@ -567,7 +616,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         TSG_CHECK(cudaStreamSynchronize(st));
         hist.assign(p_hist, p_hist + nslots);
     }
-    if (hist[nb] > 0) {
+    const int only = h->only_bin;  // >= 0: the autotuner times one bin's kernel
+    if (hist[nb] > 0 && only < 0) {
         PhaseScope ps(h, 4, st);
         const int blocks = std::min(hist[nb], h->sms);
         const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
@@ -582,20 +632,24 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         PhaseScope ps(h, 3, st);
         TSG_CHECK(cudaMemsetAsync(d_tick, 0, 4 * (nslots + 1), st));
         la.glist = d_glist;
+        BinFork fork(h, st);
         for (int b = 0; b < nb; ++b) {
-            if (hist[b] == 0) continue;
+            if (hist[b] == 0 || (only >= 0 && b != only)) continue;
             const int v = tune.bin_kernel[b];
             const int wv = num_wpb(v, dtype, wpb);
             const int tpb = teams_per_block(v, wv);
             const long long need = (hist[b] + tpb - 1) / tpb;
             const int blocks = (int)std::min<long long>(need, (long long)h->sms * h->occ_num[dtype][v]);
             la.bin = b;
-            TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wv, st));
+            TSG_CHECK(launch_num_rows(v, dtype, la, blocks, wv, fork.next()));
             ++h->launches;
         }
+        TSG_CHECK(fork.join());
         // rows the bins deferred (clustered columns, many repeats)
-        TSG_CHECK(launch_num_grouped(dtype, la, h->sms, st));
-        ++h->launches;
+        if (only < 0) {
+            TSG_CHECK(launch_num_grouped(dtype, la, h->sms, st));
+            ++h->launches;
+        }
         la.glist = nullptr;
     }
     if (tune.validate) {
@@ -673,6 +727,14 @@ spgemm_status spgemm_create(spgemm_handle** out) {
 spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (!h) return SPGEMM_OK;
     for (cudaStream_t s : h->streams_used) cudaStreamSynchronize(s);
+    for (int i = 0; i <= kMaxBins; ++i) {
+        if (h->side[i]) {
+            cudaStreamSynchronize(h->side[i]);
+            cudaStreamDestroy(h->side[i]);
+        }
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     for (const PhaseEvent& p : h->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -926,6 +988,22 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
     TSG_CHECK(launch_split_fill(dtype, X->row_ptr, X->col_idx, X->val, X->nrows, d_rb, nrp, d_cb, ncp,
                                 reinterpret_cast<const GroupDev*>(sb + o_tg), st));
     ++h->launches;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_trident_bounds(int32_t n, int32_t q, int32_t lambda, int32_t* coarse, int32_t* fine) {
+    if (n < 0 || q < 1 || lambda < 1) return SPGEMM_ERR_INVALID_ARG;
+    if ((long long)q * lambda > (1 << 20)) return SPGEMM_ERR_INVALID_ARG;
+    auto tile = [&](long long t) { return (int32_t)(t * (long long)n / q); };
+    if (coarse)
+        for (int t = 0; t <= q; ++t) coarse[t] = tile(t);
+    if (fine) {
+        for (int t = 0; t < q; ++t) {
+            const long long lo = tile(t), hi = tile(t + 1);
+            for (int sl = 0; sl < lambda; ++sl) fine[t * lambda + sl] = (int32_t)(lo + (long long)sl * (hi - lo) / lambda);
+        }
+        fine[q * lambda] = n;
+    }
     return SPGEMM_OK;
 }
 
@@ -1641,59 +1719,100 @@ spgemm_status spgemm_plan_autotune(spgemm_plan* p, const spgemm_csr_out* C, spge
             return plan_size(p, nullptr, st);
         }
     }
-    std::vector<spgemm_tune> cand;
+    // Search, per bin of the default layout (a range of row product counts),
+    // the kernel variant -- capacity and accumulator kind -- that runs that
+    // bin's rows fastest, timing the bin's kernel alone; then the warps per
+    // block of the warp variants on whole runs.  Adjacent bins that chose the
+    // same variant are merged (their threshold disappears).  Every candidate
+    // adds each output entry in the same order: the bits never change.
     spgemm_tune base;
     default_tune(&base);
-    for (int wpb : {16, 8, 32}) {
-        spgemm_tune t = base;
-        t.warps_per_block = wpb;
-        cand.push_back(t);
-    }
-    {
-        // one size up: every bin served by the next larger variant
-        spgemm_tune t = base;
-        for (int b = 0; b + 1 < t.num_bins; ++b) t.bin_kernel[b] = base.bin_kernel[b + 1];
-        cand.push_back(t);
-    }
-    {
-        // coarse: four bins
-        spgemm_tune t = base;
-        const int up[4] = {128, 512, 2048, 8192};
-        const int kv[4] = {2, 4, 6, 8};
-        t.num_bins = 4;
-        for (int b = 0; b < 4; ++b) {
-            t.bin_upper[b] = up[b];
-            t.bin_kernel[b] = kv[b];
-        }
-        cand.push_back(t);
-    }
+    base.validate = 0;
     cudaEvent_t e0, e1;
     TSG_CHECK(cudaEventCreate(&e0));
     TSG_CHECK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    spgemm_tune best_t = base;
     spgemm_status rc = SPGEMM_OK;
-    for (const spgemm_tune& t : cand) {
+    // time of one fill with tune t: whole (bin < 0) or one bin's kernel
+    auto time_fill = [&](const spgemm_tune& t, int bin, float* out_ms) -> spgemm_status {
         p->tune = t;
-        p->tune.validate = 0;
-        rc = plan_size(p, nullptr, st);
-        if (rc != SPGEMM_OK) break;
-        rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);  // warm
-        if (rc != SPGEMM_OK) break;
-        float tbest = 1e30f;
-        for (int rep = 0; rep < 3 && rc == SPGEMM_OK; ++rep) {
+        TSG_TRY(plan_size(p, nullptr, st));
+        TSG_TRY(run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st));  // warm
+        float tb = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            p->h->only_bin = bin;
             cudaEventRecord(e0, st);
-            rc = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);
+            spgemm_status r = run(p->h, p->dtype, false, p->inst, p->groups, false, nullptr, p->tune, {}, st);
             cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
+            p->h->only_bin = -1;
+            TSG_TRY(r);
+            TSG_CHECK(cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            tbest = std::min(tbest, ms);
+            tb = std::min(tb, ms);
         }
+        *out_ms = tb;
+        return SPGEMM_OK;
+    };
+    // candidate variants of a bin: the default, and every other variant of
+    // a capacity between the bin's bound and twice it (other accumulator
+    // kinds and the next sizes up)
+    auto candidates = [&](int b) {
+        std::vector<int> c{base.bin_kernel[b]};
+        for (int v = 0; v < kNumVariants; ++v) {
+            if (v == base.bin_kernel[b]) continue;
+            const int cap = variant_cap(v);
+            if (cap >= base.bin_upper[b] && cap <= 2 * base.bin_upper[b] && cap >= 32) c.push_back(v);
+        }
+        return c;
+    };
+    spgemm_tune chosen_t = base;
+    {
+        p->tune = base;
+        rc = plan_size(p, nullptr, st);
+        const std::vector<int> hist0 = p->h->plan_hist;
+        for (int b = 0; b < base.num_bins && rc == SPGEMM_OK; ++b) {
+            if (b >= (int)hist0.size() || hist0[b] == 0) continue;
+            float best_b = 1e30f;
+            for (int v : candidates(b)) {
+                spgemm_tune t = chosen_t;
+                t.bin_kernel[b] = v;
+                float ms = 0.f;
+                rc = time_fill(t, b, &ms);
+                if (rc != SPGEMM_OK) break;
+                if (ms < best_b * 0.98f || (v == base.bin_kernel[b] && ms < best_b)) {
+                    best_b = ms;
+                    chosen_t.bin_kernel[b] = v;
+                }
+            }
+        }
+    }
+    // merge neighbours that chose the same variant
+    if (rc == SPGEMM_OK) {
+        spgemm_tune m = chosen_t;
+        int nbm = 0;
+        for (int b = 0; b < chosen_t.num_bins; ++b) {
+            if (nbm > 0 && m.bin_kernel[nbm - 1] == chosen_t.bin_kernel[b]) {
+                m.bin_upper[nbm - 1] = chosen_t.bin_upper[b];
+            } else {
+                m.bin_upper[nbm] = chosen_t.bin_upper[b];
+                m.bin_kernel[nbm] = chosen_t.bin_kernel[b];
+                ++nbm;
+            }
+        }
+        m.num_bins = nbm;
+        chosen_t = m;
+    }
+    float best = 1e30f;
+    spgemm_tune best_t = chosen_t;
+    for (int wpb : {16, 8, 32}) {
         if (rc != SPGEMM_OK) break;
-        if (tbest < best) {
-            best = tbest;
-            best_t = p->tune;
+        spgemm_tune t = chosen_t;
+        t.warps_per_block = wpb;
+        float ms = 0.f;
+        rc = time_fill(t, -1, &ms);
+        if (rc == SPGEMM_OK && ms < best) {
+            best = ms;
+            best_t = t;
         }
     }
     cudaEventDestroy(e0);
@@ -1752,6 +1871,19 @@ spgemm_status spgemm_tune_cache_entry(int64_t index, uint64_t* key, spgemm_tune*
     std::advance(it, index);
     *key = it->first;
     *t = it->second;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_set_concurrent_bins(spgemm_handle* h, int32_t enable) {
+    if (!h) return SPGEMM_ERR_INVALID_ARG;
+    h->concurrent_bins = enable != 0;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_set_concurrent_bins(spgemm_plan* p, int32_t enable) {
+    if (!p) return SPGEMM_ERR_INVALID_ARG;
+    plan_drop_graph(p);
+    p->h->concurrent_bins = enable != 0;
     return SPGEMM_OK;
 }
 

@@ -105,3 +105,16 @@ def test_trident_bounds_match_oracle():
     from paper_2603_21444_gb300 import api
     for n, q, lam in [(64, 2, 2), (97, 3, 2), (2 ** 21, 4, 4), (10, 4, 3), (5, 1, 1)]:
         assert api.trident_bounds(n, q, lam) == tuple(oracle.trident_bounds(n, q, lam))
+
+
+def test_trident_bounds_host_call_matches_oracle(lib):
+    # the library's split of [0, n) (Sec. 3.2) against the oracle's, host only
+    import oracle
+    from paper_2603_21444_gb300 import api
+    for n, q, lam in [(0, 1, 1), (1, 4, 4), (17, 4, 4), (1000, 3, 2), (2**21, 4, 4), (2**31 - 1, 7, 5), (10, 16, 1)]:
+        assert api.trident_bounds(n, q, lam) == tuple(map(list, oracle.trident_bounds(n, q, lam)))
+    c = (ctypes.c_int32 * 2)()
+    assert lib.spgemm_trident_bounds(-1, 1, 1, c, None) == 1
+    assert lib.spgemm_trident_bounds(5, 0, 1, c, None) == 1
+    assert lib.spgemm_trident_bounds(5, 1, 0, None, None) == 1
+    assert lib.spgemm_trident_bounds(5, 1, 1, None, None) == 0

@@ -142,3 +142,37 @@ def test_batch_of_uneven_products(tsg, handle):
     torch.cuda.synchronize()
     for (a, b), C in zip(pairs, Cs):
         exact(C.to_host(), oracle.spgemm(a, b)[0])
+
+
+def test_concurrent_and_sequential_bins_agree(tsg, handle):
+    # the per-bin launches forked onto the handle's streams (default) and
+    # issued one after another give the same bits, direct and from a graph
+    shapes = [(1500, 60), (800, 30), (3000, 12), (1024, 64), (2500, 20), (600, 3)]
+    pairs = [(gen.er(n, n, d, 3000 + 2 * t), gen.er(n, n, d, 3001 + 2 * t)) for t, (n, d) in enumerate(shapes)]
+    As = [tsg.DeviceCSR.from_host(a) for a, _ in pairs]
+    Bs = [tsg.DeviceCSR.from_host(b) for _, b in pairs]
+    plan = tsg.Plan(As, Bs)
+    outs = []
+    for conc in (True, False, True):
+        plan.set_concurrent_bins(conc)
+        for C in plan.C:
+            C.val.zero_()
+            C.col.zero_()
+        plan.execute(False)
+        plan.execute(True)
+        Cs = plan.execute(True)
+        torch.cuda.synchronize()
+        outs.append([C.to_host() for C in Cs])
+    plan.close()
+    for (a, b), got in zip(pairs, outs[0]):
+        exact(got, oracle.spgemm(a, b)[0])
+    for other in outs[1:]:
+        for x, y in zip(outs[0], other):
+            assert all(np.array_equal(p, q) for p, q in zip(x, y))
+    # a handle's direct calls, both ways
+    handle.set_concurrent_bins(False)
+    seq = [product(tsg, a, b, handle) for a, b in pairs[:3]]
+    handle.set_concurrent_bins(True)
+    con = [product(tsg, a, b, handle) for a, b in pairs[:3]]
+    for x, y in zip(seq, con):
+        assert all(np.array_equal(p, q) for p, q in zip(x, y))
