@@ -538,40 +538,47 @@ __device__ __forceinline__ void gather_strided(const RowArgs& a, int ib, int nA,
 
 // ------------------------------------------------ symbolic, warp-team variant
 //
-// Same count as sym_row (first insertions into a shared-memory hash set of
-// 4 pow2ceil(u) slots, at most the largest power of two within 4 CAP),
-// arranged for SIMT efficiency: every product makes one
-// insertion attempt at its home slot, all slots of a lane issued together;
-// the products that met a different column there (about one in eight) are
-// compacted into a list and finish their linear probe one per lane.  The
-// meta keeps B-row offsets (4 B) instead of pointers and shares the table's
-// storage while the products are gathered.
+// nnz(C_i) = u - (products whose column an earlier product already has).
+// Every product sets one bit, chosen by a multiplicative hash of its column,
+// of a shared-memory bitmap of 64 pow2ceil(u) bits (at most kSymBitsMax); a
+// product that finds its bit already set is FLAGGED.  The first product to
+// reach a bit is never flagged, so unflagged products have pairwise distinct
+// columns (two of them would have met on one bit).  A flagged product f
+// repeats an earlier column exactly when some other product g has f's
+// column and g is unflagged, or flagged with a smaller index: in a column
+// group of m products that counts m - 1 whether or not one of them is
+// unflagged, and 0 for a lone product flagged by another column's bit.  The
+// warp checks each flagged product -- about u / 128 per row besides true
+// repeats -- against all u products with one ballot.  Exact for any hash.
+// The meta keeps B-row offsets (4 B) instead of pointers and shares the
+// bitmap's storage while the products are gathered.
+
+constexpr int kSymBitsMax = 32768;
 
 template <int CAP>
 struct WSymLayout {
     static constexpr int MAXA = CAP / 2;
-    static constexpr int TBL = 4 * CAP;
-    static constexpr int TBL2 = pow2floor_c(TBL);                  // largest table used (a power of two)
-    static constexpr int table = 0;                                // int[TBL]
-    static constexpr int clist = 4 * TBL;                          // int[CAP] collided columns
-    static constexpr int bytes = (clist + 4 * CAP + 15) & ~15;
-    static constexpr int m_pre = 0;                                // int[MAXA + 1] (aliases table)
+    static constexpr int BITS = 64 * pow2floor_c(2 * CAP - 1) < kSymBitsMax ? 64 * pow2floor_c(2 * CAP - 1)
+                                                                          : kSymBitsMax;  // 64 pow2ceil(CAP)
+    static constexpr int bm = 0;                                   // u32[BITS / 32]
+    static constexpr int m_pre = 0;                                // int[MAXA + 1] (aliases the bitmap)
     static constexpr int m_bs = m_pre + 4 * (MAXA + 1);            // int[MAXA]
     static constexpr int m_inst = m_bs + 4 * MAXA;                 // u8[MAXA]
-    static_assert(m_inst + MAXA <= clist, "meta does not fit its alias region");
+    static constexpr int alias_end = (m_inst + MAXA) > BITS / 8 ? (m_inst + MAXA) : BITS / 8;
+    static constexpr int owner = (alias_end + 15) & ~15;           // int[32] strided-gather scratch
+    static constexpr int bytes = owner + 4 * 32;
+    static_assert(BITS % 128 == 0, "bitmap cleared in 16-byte stores");
 };
 
 template <int PER>
 __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* sm) {
     constexpr int CAP = 32 * PER;
     using L = WSymLayout<CAP>;
-    int* table = reinterpret_cast<int*>(sm + L::table);
-    int* clist = reinterpret_cast<int*>(sm + L::clist);
+    unsigned* bm = reinterpret_cast<unsigned*>(sm + L::bm);
     int* m_pre = reinterpret_cast<int*>(sm + L::m_pre);
     int* m_bs = reinterpret_cast<int*>(sm + L::m_bs);
     unsigned char* m_inst = reinterpret_cast<unsigned char*>(sm + L::m_inst);
     const int lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
     const int g = unit_group(a.unit_base, a.ngroups, unit);
     const GroupDev& G = a.groups[g];
     const int rho = (int)(unit - a.unit_base[g]);
@@ -595,54 +602,46 @@ __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* s
         float unused_val[PER];
         int unused_ins[PER];
         if (use_strided<PER>(nA, u))
-            gather_strided<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, clist, lane, col,
-                                              unused_val, unused_ins);
+            gather_strided<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst,
+                                              reinterpret_cast<int*>(sm + L::owner), lane, col, unused_val,
+                                              unused_ins);
         else
             gather_chunks<PER, false, float>(a, ib, nA, u, m_pre, m_bs, nullptr, m_inst, lane, col, unused_val,
                                              unused_ins);
     }
-    __syncwarp();  // the meta is dead: the table takes its place
-    const int T2 = min(4 * pow2ceil(u), L::TBL2);
-    const int shift = 32 - (31 - __clz(T2));
-    for (int i = 4 * lane; i < T2; i += 128) *reinterpret_cast<int4*>(table + i) = make_int4(-1, -1, -1, -1);
+    __syncwarp();  // the meta is dead: the bitmap takes its place
+    const int nbits = min(64 * pow2ceil(u), L::BITS);
+    const int shift = 32 - (31 - __clz(nbits));
+    for (int i = 4 * lane; i < nbits / 32; i += 128) *reinterpret_cast<int4*>(bm + i) = make_int4(0, 0, 0, 0);
     __syncwarp();
-
-    // one attempt per product at its home slot
-    int fresh = 0, ncol = 0;
-    int old[PER];
+    unsigned flagged = 0;  // bit s: the lane's product in slot s found its bit set
 #pragma unroll
-    for (int s = 0; s < PER; ++s) {
-        old[s] = -1;
-        if (col[s] >= 0) old[s] = atomicCAS(&table[((unsigned)col[s] * 0x9E3779B1u) >> shift], -1, col[s]);
-    }
-#pragma unroll
-    for (int s = 0; s < PER; ++s) {
-        const bool hit = col[s] >= 0 && old[s] == -1;
-        const bool clash = col[s] >= 0 && old[s] != -1 && old[s] != col[s];
-        fresh += hit;
-        const unsigned m = __ballot_sync(0xffffffffu, clash);
-        if (clash) clist[ncol + __popc(m & lt)] = col[s];
-        ncol += __popc(m);
-    }
-    __syncwarp();
-    // the collided products continue their probe, one per lane
-    bool overflow = false;
-    for (int w = lane; w < ncol; w += 32) {
-        const int c = clist[w];
-        unsigned h = ((((unsigned)c * 0x9E3779B1u) >> shift) + 1) & (T2 - 1);
-        int probe = 1;
-        for (; probe < T2; ++probe) {
-            const int o = atomicCAS(&table[h], -1, c);
-            if (o == -1) { ++fresh; break; }
-            if (o == c) break;
-            h = (h + 1) & (T2 - 1);
+    for (int s = 0; s < PER; ++s)
+        if (col[s] >= 0) {
+            const unsigned h = ((unsigned)col[s] * 0x9E3779B1u) >> shift;
+            const unsigned bit = 1u << (h & 31);
+            if (atomicOr(bm + (h >> 5), bit) & bit) flagged |= 1u << s;
         }
-        overflow |= probe == T2;
-    }
-    if (overflow) atomicOr(a.status, kStatusHashOverflow);
+    // each flagged product against every product of the row (index s * 32 + lane)
+    int dup = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
-    if (lane == 0) a.counts[unit] = fresh;
+    for (int s = 0; s < PER; ++s) {
+        unsigned m = __ballot_sync(0xffffffffu, (flagged >> s) & 1u);
+        while (m) {
+            const int fl = __ffs(m) - 1;
+            m &= m - 1;
+            const int cf = __shfl_sync(0xffffffffu, col[s], fl);
+            const int idf = 32 * s + fl;
+            bool hit = false;
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int id = 32 * t + lane;
+                hit |= col[t] == cf && id != idf && (((flagged >> t) & 1u) == 0 || id < idf);
+            }
+            dup += __any_sync(0xffffffffu, hit) ? 1 : 0;
+        }
+    }
+    if (lane == 0) a.counts[unit] = u - dup;
     __syncwarp();
 }
 
