@@ -105,6 +105,9 @@ typedef struct {
  *   8: 512 threads, 8192   9: warp, 384   10: one thread per row, 16
  *   11: 128 threads, 1024  12: 256 threads, 2048  13: 512 threads, 4096
  *   14: 1024 threads, 8192   15: warp, 320
+ *   16-19: the block teams 11-14 with the row's B segments staged in shared
+ *   memory by TMA bulk copies (rows of at most 128 A entries; others read
+ *   from global memory as in 11-14)
  * Two accumulator kinds serve the block teams: variants 5-8 sort 64-bit
  * (column, product) keys by bucket and rank inside each bucket; variants
  * 11-14 keep the products in registers and run the warp teams' counting sort
@@ -115,7 +118,7 @@ typedef struct {
  * variants 10, 0, 1, 2, 3, 15, 9, 4, 11, 12, 13, 14.  A variant whose
  * capacity is below bin_upper is rejected. */
 #define SPGEMM_MAX_BINS 12
-#define SPGEMM_NUM_VARIANTS 16
+#define SPGEMM_NUM_VARIANTS 20
 enum { SPGEMM_ACC_SORT = 0 };
 
 typedef struct {

@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtrident_spgemm.so")
 
 MAX_BINS = 12
-NUM_VARIANTS = 16
+NUM_VARIANTS = 20
 NUM_PHASES = 8
 F32, F64 = 0, 1
 

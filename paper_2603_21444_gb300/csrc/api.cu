@@ -774,7 +774,7 @@ spgemm_status spgemm_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const sp
                               int64_t* c_nnz, spgemm_stream_t stream) {
     if (!h || !csr_in_ok(A, false) || !csr_in_ok(B, false) || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
     if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
-    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val, B->nnz}};
     std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, c_row_ptr, nullptr, nullptr, 0}};
     std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
@@ -786,7 +786,7 @@ spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_
     if (!h || !csr_in_ok(A, true) || !csr_in_ok(B, true) || !C || !C->row_ptr) return SPGEMM_ERR_INVALID_ARG;
     if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
     if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
-    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val, B->nnz}};
     std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val, 0}};
     std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
@@ -798,7 +798,7 @@ spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const sp
                               spgemm_stream_t stream) {
     if (!h || !csr_in_ok(A, false) || !csr_in_ok(B, false) || !total) return SPGEMM_ERR_INVALID_ARG;
     if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
-    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val, B->nnz}};
     std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, nullptr, nullptr, nullptr, 0}};
     return run(h, 0, false, inst, groups, false, total, h->tune, {}, reinterpret_cast<cudaStream_t>(stream), -1, true);
 }
@@ -811,7 +811,7 @@ spgemm_status spgemm_fused(spgemm_handle* h, spgemm_dtype dtype, const spgemm_cs
     if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
     if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val}};
+    std::vector<InstDev> inst{{A->row_ptr, A->col_idx, A->val, B->row_ptr, B->col_idx, B->val, B->nnz}};
     std::vector<GroupDev> groups{{0, 1, A->nrows, B->ncols, C->row_ptr, C->col_idx, C->val, 0}};
     std::vector<Validate> checks{{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz},
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
@@ -835,7 +835,7 @@ spgemm_status spgemm_merge(spgemm_handle* h, spgemm_dtype dtype, int32_t nparts,
         const spgemm_csr_in* P = parts + t;
         if (!csr_in_ok(P, !sizing)) return SPGEMM_ERR_INVALID_ARG;
         if (P->nrows != C->nrows || P->ncols != C->ncols) return SPGEMM_ERR_SHAPE;
-        inst.push_back({nullptr, nullptr, nullptr, P->row_ptr, P->col_idx, P->val});
+        inst.push_back({nullptr, nullptr, nullptr, P->row_ptr, P->col_idx, P->val, P->nnz});
         checks.push_back({P->row_ptr, P->col_idx, P->nrows, P->ncols, P->nnz});
     }
     if (!sizing && !C->val) return SPGEMM_ERR_INVALID_ARG;
@@ -878,7 +878,7 @@ spgemm_status spgemm_batched(spgemm_handle* h, spgemm_dtype dtype, int32_t ninst
                           sizing ? nullptr : Cg.val, 0});
     }
     for (int t = 0; t < ninst; ++t) {
-        inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val});
+        inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val, B[t].nnz});
         if (tn.validate) {
             checks.push_back({A[t].row_ptr, A[t].col_idx, A[t].nrows, A[t].ncols, A[t].nnz});
             checks.push_back({B[t].row_ptr, B[t].col_idx, B[t].nrows, B[t].ncols, B[t].nnz});
@@ -1631,7 +1631,7 @@ spgemm_status spgemm_plan_create(spgemm_dtype dtype, int32_t ninst, const spgemm
         p->groups.push_back({t0, t1 - t0, A[t0].nrows, B[t0].ncols, c_row_ptr[g], nullptr, nullptr, 0});
     }
     for (int t = 0; t < ninst; ++t)
-        p->inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val});
+        p->inst.push_back({A[t].row_ptr, A[t].col_idx, A[t].val, B[t].row_ptr, B[t].col_idx, B[t].val, B[t].nnz});
     spgemm_status rc = spgemm_create(&p->h);
     if (rc == SPGEMM_OK) rc = plan_size(p, c_nnz, reinterpret_cast<cudaStream_t>(stream));
     if (rc != SPGEMM_OK) {

@@ -25,6 +25,7 @@ struct InstDev {
     const int* brp;     // B_t row_ptr (merge mode: the partial's row_ptr)
     const int* bcol;    // B_t col_idx
     const void* bval;   // B_t values
+    long long bnnz;     // entries of bcol / bval (bulk copies stay inside them)
 };
 
 struct GroupDev {
@@ -48,10 +49,13 @@ struct GroupDev {
 // sits between 3 and 9: rows just above 256 products (the trident grid's
 // rows scatter around 256) without the 384 variant's register and shared
 // memory cost.
-constexpr int kNumVariants = 16;
-__host__ __device__ constexpr bool variant_is_team(int v) { return v >= 11 && v <= 14; }
+// Variants 16-19 are the block teams 11-14 with their B rows staged in
+// shared memory by TMA bulk copies (rows_team.cuh).
+constexpr int kNumVariants = 20;
+__host__ __device__ constexpr bool variant_is_staged(int v) { return v >= 16 && v <= 19; }
+__host__ __device__ constexpr bool variant_is_team(int v) { return (v >= 11 && v <= 14) || variant_is_staged(v); }
 __host__ __device__ constexpr int variant_team(int v) {
-    return variant_is_team(v) ? (128 << (v - 11))
+    return variant_is_team(v) ? (128 << (variant_is_staged(v) ? v - 16 : v - 11))
                               : (v == 10 ? 1 : ((v <= 4 || v == 9 || v == 15) ? 32
                                                                              : (v == 5 ? 128 : (v == 6 ? 256 : 512))));
 }

@@ -31,6 +31,7 @@ struct VariantShape {
     static constexpr int PER = variant_per(V);
     static constexpr int CAP = TEAM * PER;
     static constexpr bool TEAMK = variant_is_team(V);  // block team running the warp counting sort
+    static constexpr bool STAGED = variant_is_staged(V);  // ... with its B rows staged by TMA
 };
 
 // Calls f(std::integral_constant-like tag) for the runtime variant v.
@@ -53,6 +54,10 @@ inline cudaError_t dispatch_variant(int v, F&& f) {
         case 13: return f(VariantShape<13>());
         case 14: return f(VariantShape<14>());
         case 15: return f(VariantShape<15>());
+        case 16: return f(VariantShape<16>());
+        case 17: return f(VariantShape<17>());
+        case 18: return f(VariantShape<18>());
+        case 19: return f(VariantShape<19>());
         default: return cudaErrorInvalidValue;
     }
 }

@@ -12,7 +12,7 @@ static int num_smem_bytes_t(int variant, int wpb) {
         if constexpr (SS::TEAM == 1)
             bytes = ThreadNumLayout<T>::bytes;
         else if constexpr (SS::TEAMK)
-            bytes = TNumLayout<SS::CAP, T>::bytes;
+            bytes = SS::STAGED ? TNumLayout<SS::CAP, T>::bytes_staged : TNumLayout<SS::CAP, T>::bytes;
         else
             bytes = SS::TEAM == 32 ? WNumLayout<SS::CAP, T>::bytes * wpb : NumLayout<SS::CAP, T>::bytes;
         return cudaSuccess;
@@ -32,7 +32,7 @@ static int num_blocks_per_sm_t(int variant, int wpb) {
         if constexpr (SS::TEAM == 1) {
             nb = blocks_per_sm(k_num_thread<T>, kThreadRows, ThreadNumLayout<T>::bytes);
         } else if constexpr (SS::TEAMK) {
-            nb = blocks_per_sm(k_num_team<SS::TEAM / 32, T>, SS::TEAM, TNumLayout<SS::CAP, T>::bytes);
+            nb = blocks_per_sm(k_num_team<SS::TEAM / 32, T, SS::STAGED>, SS::TEAM, num_smem_bytes_t<T>(variant, wpb));
         } else {
             const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
             nb = blocks_per_sm(k_num_rows<SS::TEAM, SS::PER, T>, threads, num_smem_bytes_t<T>(variant, wpb));
@@ -56,9 +56,10 @@ static cudaError_t launch_num_rows_t(int variant, const RowLaunchArgs& l, int bl
             cudaFuncSetAttribute(k_num_thread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             k_num_thread<T><<<blocks, kThreadRows, smem, s>>>(a);
         } else if constexpr (SS::TEAMK) {
-            const int smem = TNumLayout<SS::CAP, T>::bytes;
-            cudaFuncSetAttribute(k_num_team<SS::TEAM / 32, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k_num_team<SS::TEAM / 32, T><<<blocks, SS::TEAM, smem, s>>>(a);
+            const int smem = num_smem_bytes_t<T>(variant, wpb);
+            cudaFuncSetAttribute(k_num_team<SS::TEAM / 32, T, SS::STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+            k_num_team<SS::TEAM / 32, T, SS::STAGED><<<blocks, SS::TEAM, smem, s>>>(a);
         } else {
             const int threads = SS::TEAM == 32 ? 32 * wpb : SS::TEAM;
             const int smem = num_smem_bytes_t<T>(variant, wpb);

@@ -30,6 +30,7 @@
 namespace tsg {
 
 constexpr int kTeamPer = 8;  // products per thread
+constexpr int kStageMaxA = 128;  // staged rows: at most this many A entries
 
 template <int CAP, typename T>
 struct TNumLayout {
@@ -44,6 +45,18 @@ struct TNumLayout {
     static constexpr int ctl = (wl + CAP + 15) & ~15;              // int[kCtl]
     static constexpr int kCtl = 96;
     static constexpr int bytes = ctl + 4 * kCtl;
+    // staged variant only (after `bytes`): the meta of rows of at most
+    // kStageMaxA A entries, their staging offsets, and the copy barrier; the
+    // staged B rows themselves occupy [ocol, wl)
+    static constexpr int s_a = (bytes + 15) & ~15;                 // T[kStageMaxA]
+    static constexpr int s_pre = s_a + (int)sizeof(T) * kStageMaxA;  // int[kStageMaxA + 1]
+    static constexpr int s_bs = s_pre + 4 * (kStageMaxA + 1);      // int[kStageMaxA]
+    static constexpr int s_offc = s_bs + 4 * kStageMaxA;           // int[kStageMaxA] staged column offset
+    static constexpr int s_offv = s_offc + 4 * kStageMaxA;         // int[kStageMaxA] staged value offset
+    static constexpr int s_inst = s_offv + 4 * kStageMaxA;         // u8[kStageMaxA]
+    static constexpr int s_bar = (s_inst + kStageMaxA + 15) & ~15; // u64 mbarrier
+    static constexpr int bytes_staged = s_bar + 16;
+    static constexpr int stage_bytes = wl - ocol;                  // room for the staged B rows
     // ctl words: [0, 34) scan scratch, 40 row ticket, 41 listed buckets,
     // [48, 48 + 32) heads per warp
     static constexpr int c_ticket = 40, c_nwl = 41, c_heads = 48;
@@ -55,7 +68,7 @@ struct TNumLayout {
     static_assert((CAP & (CAP - 1)) == 0, "team capacity must be a power of two");
     static_assert(m_inst + MAXA <= wl, "meta does not fit its alias region");
     static_assert((oval & 7) == 0, "value array alignment");
-    static_assert(bytes <= 227 * 1024, "team layout exceeds shared memory");
+    static_assert(bytes_staged <= 227 * 1024, "team layout exceeds shared memory");
 };
 
 // Row meta of a block team: per A entry (instances in order, entries in
@@ -102,8 +115,124 @@ __device__ __forceinline__ void team_meta(const RowArgs& a, int ib, int icount, 
     __syncthreads();
 }
 
-template <int NW, typename T>
-__device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* sm) {
+// ------------------------------------------------ TMA staging of B rows
+//
+// The staged variant (STAGED) copies every B row segment a row reads into
+// shared memory with one 1D bulk copy (cp.async.bulk, no multicast) per
+// array and A entry, completing on an mbarrier, and gathers the products
+// from shared memory.  A bulk copy moves 16-byte units between 16-byte
+// aligned addresses, so each segment is copied from the 16-byte boundary at
+// or below its start to the one at or above its end, into its own slot
+// (16-byte aligned, 48 bytes of slack per entry keeps slots apart: slot t of
+// the columns starts at align16(4 pre_t + 48 t), of the values at
+// align16(size(T) pre_t + 48 t)), and read at the start's offset within its
+// 16 bytes.  A row is staged when it has at most kStageMaxA A entries, its
+// slots fit [ocol, wl), and every rounded segment lies inside its array;
+// otherwise it is gathered from global memory as in the plain variant.  The
+// barrier wait is bounded: past kStageSpinLimit polls the row is abandoned
+// with kStatusTimeout latched (its products dropped, every write in bounds).
+
+constexpr unsigned kStageSpinLimit = 1u << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one arrival that also expects `bytes` of bulk copies in the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The lane's products [pbase + 4 (32 c + lane), + 4) from the staged slots.
+template <int PER, typename T>
+__device__ __forceinline__ void gather_staged(const char* stage, const int* s_pre, const int* s_offc, const int* s_offv,
+                                              const T* s_a, const unsigned char* s_inst, bool merge, int nA, int u,
+                                              int lane, int pbase, int (&col)[PER], T (&val)[PER], int (&ins)[PER]) {
+    static_assert(PER % 4 == 0, "chunks of four");
+#pragma unroll
+    for (int c = 0; c < PER / 4; ++c) {
+        const int p0 = pbase + 4 * (32 * c + lane);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            col[4 * c + v] = -1;
+            val[4 * c + v] = T(0);
+            ins[4 * c + v] = 0;
+        }
+        if (p0 >= u) continue;
+        int t = owner_of(s_pre, nA, p0);
+        int tb = s_pre[t], te = s_pre[t + 1];
+        int oc = s_offc[t], ov = s_offv[t];
+        T av = s_a[t];
+        int ti = s_inst[t];
+        const int j0 = p0 - tb;
+        if (p0 + 4 <= te && ((oc + 4 * j0) & 15) == 0 && ((ov + (int)sizeof(T) * j0) & 15) == 0) {
+            const int4 cc = *reinterpret_cast<const int4*>(stage + oc + 4 * j0);
+            T bv[4];
+            if (sizeof(T) == 8) {
+                const double2 x = *reinterpret_cast<const double2*>(stage + ov + 8 * j0);
+                const double2 y = *reinterpret_cast<const double2*>(stage + ov + 8 * j0 + 16);
+                bv[0] = (T)x.x; bv[1] = (T)x.y; bv[2] = (T)y.x; bv[3] = (T)y.y;
+            } else {
+                const float4 x = *reinterpret_cast<const float4*>(stage + ov + 4 * j0);
+                bv[0] = (T)x.x; bv[1] = (T)x.y; bv[2] = (T)x.z; bv[3] = (T)x.w;
+            }
+            col[4 * c + 0] = cc.x;
+            col[4 * c + 1] = cc.y;
+            col[4 * c + 2] = cc.z;
+            col[4 * c + 3] = cc.w;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                val[4 * c + v] = merge ? bv[v] : mul_rn(av, bv[v]);
+                ins[4 * c + v] = ti;
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int p = p0 + v;
+                if (p < u) {
+                    while (p >= te) {
+                        ++t;
+                        tb = te;
+                        te = s_pre[t + 1];
+                        oc = s_offc[t];
+                        ov = s_offv[t];
+                        av = s_a[t];
+                        ti = s_inst[t];
+                    }
+                    const int j = p - tb;
+                    col[4 * c + v] = *reinterpret_cast<const int*>(stage + oc + 4 * j);
+                    const T bv = *reinterpret_cast<const T*>(stage + ov + (int)sizeof(T) * j);
+                    val[4 * c + v] = merge ? bv : mul_rn(av, bv);
+                    ins[4 * c + v] = ti;
+                }
+            }
+        }
+    }
+}
+
+template <int NW, typename T, bool STAGED = false>
+__device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* sm, unsigned* parity = nullptr) {
     constexpr int NT = 32 * NW;
     constexpr int PER = kTeamPer;
     constexpr int CAP = NT * PER;
@@ -130,8 +259,37 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
     const int ib = G.inst_begin, icount = G.inst_count;
     const bool multi = a.merge || icount > 1;
 
+    // staged variant: rows of few A entries keep their meta outside the
+    // staging area
+    bool small = false;
+    if (STAGED) {
+        int na = 0;
+        for (int t = 0; t < icount; ++t) {
+            if (a.merge) {
+                ++na;
+            } else {
+                const InstDev& I = a.inst[ib + t];
+                na += __ldg(I.arp + rho + 1) - __ldg(I.arp + rho);
+            }
+        }
+        small = na <= kStageMaxA;
+        if (small) {
+            m_pre = reinterpret_cast<int*>(sm + L::s_pre);
+            m_bs = reinterpret_cast<int*>(sm + L::s_bs);
+            m_a = reinterpret_cast<T*>(sm + L::s_a);
+            m_inst = reinterpret_cast<unsigned char*>(sm + L::s_inst);
+        }
+    }
     int nA, u;
-    team_meta<NT, T, L::MAXA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, nA, u);
+    if (STAGED && small)
+        team_meta<NT, T, kStageMaxA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, nA, u);
+    else
+        team_meta<NT, T, L::MAXA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, nA, u);
+    if (STAGED && small && nA > kStageMaxA) {  // the inputs changed under us
+        if (tid == 0) atomicOr(a.status, kStatusInternal);
+        __syncthreads();
+        return;
+    }
     if (nA > L::MAXA || u > CAP) {  // the binning rules this out unless the inputs changed
         if (tid == 0) atomicOr(a.status, kStatusInternal);
         __syncthreads();
@@ -154,13 +312,83 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
     const bool distinct = row_len == u;  // no repeated column: sort only
     __syncthreads();
 
+    // ---- staging (staged variant): one bulk copy per A entry and array
+    bool staged = false;
+    if (STAGED && small) {
+        int* s_offc = reinterpret_cast<int*>(sm + L::s_offc);
+        int* s_offv = reinterpret_cast<int*>(sm + L::s_offv);
+        unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + L::s_bar);
+        bool ok = true;
+        uintptr_t csrc = 0, vsrc = 0;
+        unsigned cbytes = 0, vbytes = 0;
+        int oc = 0, ov = 0;
+        if (tid < nA) {
+            const InstDev& I = a.inst[ib + m_inst[tid]];
+            const int len = m_pre[tid + 1] - m_pre[tid];
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(I.bcol), vb = reinterpret_cast<uintptr_t>(I.bval);
+            const uintptr_t ca = cb + 4ull * (unsigned)m_bs[tid], va = vb + sizeof(T) * (unsigned)m_bs[tid];
+            csrc = ca & ~uintptr_t(15);
+            vsrc = va & ~uintptr_t(15);
+            const uintptr_t cend = (ca + 4ull * len + 15) & ~uintptr_t(15);
+            const uintptr_t vend = (va + sizeof(T) * len + 15) & ~uintptr_t(15);
+            ok = csrc >= cb && vsrc >= vb && cend <= cb + 4ull * (unsigned long long)I.bnnz &&
+                 vend <= vb + sizeof(T) * (unsigned long long)I.bnnz;
+            cbytes = len > 0 ? (unsigned)(cend - csrc) : 0u;
+            vbytes = len > 0 ? (unsigned)(vend - vsrc) : 0u;
+            const int c0 = (4 * m_pre[tid] + 48 * tid + 15) & ~15;
+            const int v0 = ((int)sizeof(T) * m_pre[tid] + 48 * tid + 15) & ~15;
+            oc = c0 + (int)(ca - csrc);
+            ov = v0 + (int)(va - vsrc);
+            s_offc[tid] = oc;
+            s_offv[tid] = ov;
+        }
+        // the column slots, then the value slots, inside [ocol, wl)
+        const int cspan = (4 * u + 48 * nA + 15 + 15) & ~15;
+        const int vspan = ((int)sizeof(T) * u + 48 * nA + 15 + 15) & ~15;
+        staged = __syncthreads_and(ok) && cspan + vspan <= L::stage_bytes;
+        int total = 0;
+        if (staged) Team<NT>::scan_excl((int)(cbytes + vbytes), &total, ctl);
+        staged = staged && total > 0;
+        if (staged) {
+            char* stage = sm + L::ocol;
+            // earlier generic accesses to the slots come before the copies;
+            // the barrier expects every byte before any copy is issued
+            fence_proxy_async_smem();
+            if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)total);
+            __syncthreads();
+            if (tid < nA) {
+                if (cbytes) bulk_g2s(stage + (oc & ~15), reinterpret_cast<const void*>(csrc), cbytes, bar);
+                if (vbytes) bulk_g2s(stage + cspan + (ov & ~15), reinterpret_cast<const void*>(vsrc), vbytes, bar);
+            }
+            unsigned spins = 0;
+            bool done = false;
+            while (!(done = mbar_try_wait(bar, *parity)) && ++spins < kStageSpinLimit) {
+            }
+            done = __syncthreads_and(done);
+            *parity ^= 1u;
+            if (!done) {
+                if (tid == 0) atomicOr(a.status, kStatusTimeout);
+                staged = false;
+                u = 0;  // abandon the row's products
+            }
+            // the value slots follow the column slots
+            if (tid < nA) s_offv[tid] += cspan;
+            __syncthreads();
+        }
+    }
+
     // ---- gather: warp w, products [256 w, 256 w + 256), chunked
     int col[PER];
     T val[PER];
     int hh[PER];  // slot in bucket (low 16 bits) | instance << 16
     {
         int ins[PER];
-        gather_chunks<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, lane, col, val, ins, 32 * PER * w);
+        if (STAGED && staged)
+            gather_staged<PER, T>(sm + L::ocol, m_pre, reinterpret_cast<const int*>(sm + L::s_offc),
+                                  reinterpret_cast<const int*>(sm + L::s_offv), m_a, m_inst, a.merge, nA, u, lane,
+                                  32 * PER * w, col, val, ins);
+        else
+            gather_chunks<PER, true, T>(a, ib, nA, u, m_pre, m_bs, m_a, m_inst, lane, col, val, ins, 32 * PER * w);
 #pragma unroll
         for (int e = 0; e < PER; ++e) hh[e] = ins[e] << 16;
     }
@@ -347,12 +575,17 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
 }
 
 // at most 64 registers per thread: 1024 threads' worth of blocks per SM
-template <int NW, typename T>
+template <int NW, typename T, bool STAGED = false>
 __global__ void __launch_bounds__(32 * NW, (32 / NW) < 1 ? 1 : (32 / NW)) k_num_team(RowArgs a) {
     extern __shared__ __align__(16) char smem[];
     using L = TNumLayout<32 * NW * kTeamPer, T>;
     int* ctl = reinterpret_cast<int*>(smem + L::ctl);
     const int begin = a.bin_off[a.bin], end = a.bin_off[a.bin + 1];
+    unsigned parity = 0;
+    if (STAGED) {
+        if (threadIdx.x == 0) mbar_init(reinterpret_cast<unsigned long long*>(smem + L::s_bar), 1);
+        __syncthreads();
+    }
     // rows by ticket; the next ticket is drawn while the current row runs
     if (threadIdx.x == 0) ctl[L::c_ticket] = atomicAdd(a.tick + a.bin, 1);
     __syncthreads();
@@ -361,7 +594,7 @@ __global__ void __launch_bounds__(32 * NW, (32 / NW) < 1 ? 1 : (32 / NW)) k_num_
         if (i >= end) break;  // the same in every thread
         __syncthreads();      // everyone has read the ticket
         if (threadIdx.x == 0) ctl[L::c_ticket] = atomicAdd(a.tick + a.bin, 1);
-        num_row_team<NW, T>(a, __ldg(a.list + i), smem);  // ends with a block barrier
+        num_row_team<NW, T, STAGED>(a, __ldg(a.list + i), smem, &parity);  // ends with a block barrier
     }
 }
 

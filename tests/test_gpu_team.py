@@ -1,5 +1,6 @@
 """GPU parity of the block-team counting-sort variants (11-14: 128, 256, 512
-and 1024 threads holding 1024, 2048, 4096 and 8192 products of a row) against
+and 1024 threads holding 1024, 2048, 4096 and 8192 products of a row; 16-19:
+the same with the row's B segments staged in shared memory by TMA) against
 the CPU oracle (Sec. 2's row-wise product): patterns and values bit for bit,
 in product, multi-instance (trident) and merge mode, with and without
 repeated columns, with one bucket per column (narrow outputs), and against
@@ -13,8 +14,9 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-TEAM = {11: 1024, 12: 2048, 13: 4096, 14: 8192}
-RANK = {11: 5, 12: 6, 13: 7, 14: 8}
+TEAM = {11: 1024, 12: 2048, 13: 4096, 14: 8192, 16: 1024, 17: 2048, 18: 4096, 19: 8192}
+RANK = {11: 5, 12: 6, 13: 7, 14: 8, 16: 5, 17: 6, 18: 7, 19: 8}
+STAGED = (16, 17, 18, 19)  # B rows staged in shared memory by TMA bulk copies
 
 
 @pytest.fixture(scope="module")
@@ -176,3 +178,48 @@ def test_concurrent_and_sequential_bins_agree(tsg, handle):
     con = [product(tsg, a, b, handle) for a, b in pairs[:3]]
     for x, y in zip(seq, con):
         assert all(np.array_equal(p, q) for p, q in zip(x, y))
+
+
+@pytest.mark.parametrize("variant", STAGED)
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_staged_variants_ragged_b_rows(tsg, handle, variant, dtype):
+    # B rows of every length 0..40 (so every start and end alignment, empty
+    # rows, and the arrays' last row), A rows of up to 128 entries (staged)
+    # and some longer (gathered from global memory)
+    cap = TEAM[variant]
+    B = gen.er_variable(3000, 5000, 40, variant, dtype, "normal", p_empty=0.05)
+    lens = np.concatenate([np.arange(1, 129, 3), [129, 200, 300], [2999, 2998]])
+    A = rows_of_lengths(lens, 3000, variant + 50, dtype)
+    # rows beyond the variant's capacity are emptied
+    u = oracle.row_products(A, B)
+    lens_kept = np.where(u <= cap, np.diff(A.rowptr), 0)
+    mask = np.repeat(u <= cap, np.diff(A.rowptr))
+    rp = np.zeros(A.nrows + 1, dtype=np.int64)
+    np.cumsum(lens_kept, out=rp[1:])
+    A = gen.CSR(A.nrows, A.ncols, rp, A.col[mask], A.val[mask])
+    prec = "f32" if dtype == np.float32 else "f64"
+    handle.set_tune(one_bin(tsg, cap, variant))
+    got = product(tsg, A, B, handle, dtype)
+    handle.set_tune(None)
+    exact(got, oracle.spgemm(A, B, prec)[0])
+
+
+def test_staged_variant_merge_and_trident(tsg, handle):
+    # merge mode (partials as B rows) and multi-instance rows on a staged variant
+    parts = [gen.er_variable(1200, 40000, 300 + 40 * t, 80 + t, np.float64, "normal", p_empty=0.05) for t in range(4)]
+    handle.set_tune(one_bin(tsg, 2048, 17))
+    C = tsg.merge([tsg.DeviceCSR.from_host(P) for P in parts], handle)
+    torch.cuda.synchronize()
+    exact(C.to_host(), oracle.csr_sum(parts))
+    A = gen.er(3000, 3000, 48, 73)
+    B = gen.er(3000, 3000, 48, 74)
+    plan = tsg.TridentPlan(tsg.DeviceCSR.from_host(A), tsg.DeviceCSR.from_host(B), 3, 2, handle)
+    t = one_bin(tsg, 2048, 17)
+    blocks = tsg.Plan(plan.As, plan.Bs, plan.group_ptr, tune=t).execute(True)
+    torch.cuda.synchronize()
+    handle.set_tune(None)
+    ref, _ = oracle.trident_product(A, B, 3, 2)
+    for i in range(3):
+        for j in range(3):
+            for k in range(2):
+                exact(blocks[plan.block_index(i, j, k)].to_host(), ref[i][j][k])
