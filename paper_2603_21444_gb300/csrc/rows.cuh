@@ -316,6 +316,17 @@ __device__ __forceinline__ void gather_chunks(const RowArgs& a, int ib, int nA, 
             }
 #pragma unroll
             for (int v = 0; v < W; ++v) ins[W * c + v] = ti;
+        } else if (W == 4 && p0 + 4 <= te) {
+            // one B row, not 16-byte aligned: four independent element loads
+#pragma unroll
+            for (int v = 0; v < W; ++v) {
+                col[W * c + v] = __ldg(bcol + f0 + v);
+                if (VALS) {
+                    const T bv = __ldg(bval + f0 + v);
+                    val[W * c + v] = a.merge ? bv : mul_rn(av, bv);
+                }
+                ins[W * c + v] = ti;
+            }
         } else {
 #pragma unroll
             for (int v = 0; v < W; ++v) {

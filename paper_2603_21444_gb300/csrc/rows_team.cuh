@@ -43,7 +43,7 @@ struct TNumLayout {
     static constexpr int oinst = op + 2 * CAP;                     // u8[CAP]
     static constexpr int wl = (oinst + CAP + 3) & ~3;              // u16[CAP / 2] buckets to sort
     static constexpr int ctl = (wl + CAP + 15) & ~15;              // int[kCtl]
-    static constexpr int kCtl = 96;
+    static constexpr int kCtl = 128;
     static constexpr int bytes = ctl + 4 * kCtl;
     // staged variant only (after `bytes`): the meta of rows of at most
     // kStageMaxA A entries, their staging offsets, and the copy barrier; the
@@ -57,9 +57,10 @@ struct TNumLayout {
     static constexpr int s_bar = (s_inst + kStageMaxA + 15) & ~15; // u64 mbarrier
     static constexpr int bytes_staged = s_bar + 16;
     static constexpr int stage_bytes = wl - ocol;                  // room for the staged B rows
-    // ctl words: [0, 34) scan scratch, 40 row ticket, 41 listed buckets,
+    // ctl words: [0, 32) and [96, 128) scan scratch (two slots used in
+    // turn), 40 / 42 row tickets (used in turn), 41 listed buckets,
     // [48, 48 + 32) heads per warp
-    static constexpr int c_ticket = 40, c_nwl = 41, c_heads = 48;
+    static constexpr int c_ticket = 40, c_nwl = 41, c_heads = 48, c_scan2 = 96;
     // meta, aliased over [ocol, wl) while the products are gathered
     static constexpr int m_pre = ocol;                             // int[MAXA + 1]
     static constexpr int m_bs = m_pre + 4 * (MAXA + 1);            // int[MAXA]
@@ -71,16 +72,47 @@ struct TNumLayout {
     static_assert(bytes_staged <= 227 * 1024, "team layout exceeds shared memory");
 };
 
+// Exclusive prefix sum over the block with a single barrier: each warp's
+// total goes to scratch[w], then every warp scans the NW totals itself.
+// scratch is read after the barrier, so it must not be written again before
+// every thread has passed a later block barrier: consecutive calls without
+// one in between alternate between two scratch slots.
+template <int NT>
+__device__ __forceinline__ int team_scan1(int v, int* total, int* scratch) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[w] = x;
+    __syncthreads();
+    const int t = lane < NW ? scratch[lane] : 0;
+    int z = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+    }
+    const int before = __shfl_sync(0xffffffffu, z - t, w);
+    *total = __shfl_sync(0xffffffffu, z, NW - 1);
+    return before + x - v;
+}
+
 // Row meta of a block team: per A entry (instances in order, entries in
 // stored order) its first product, B-row offset, a_ik and instance; nA and
 // u for the row (the same in every thread).  Entries beyond MAXA are counted
 // but not stored (the caller rejects the row).  Ends with a block barrier.
 template <int NT, typename T, int MAXA>
 __device__ __forceinline__ void team_meta(const RowArgs& a, int ib, int icount, int rho, int* m_pre, int* m_bs,
-                                          T* m_a, unsigned char* m_inst, int* scratch, int& nA, int& u) {
+                                          T* m_a, unsigned char* m_inst, int* scratch, int* scratch2, int& nA,
+                                          int& u) {
     const int tid = threadIdx.x;
     nA = 0;
     u = 0;
+    int calls = 0;
     for (int t = 0; t < icount; ++t) {
         const InstDev& I = a.inst[ib + t];
         int a0 = 0, a1 = 1;
@@ -100,7 +132,7 @@ __device__ __forceinline__ void team_meta(const RowArgs& a, int ib, int icount, 
                 if (!a.merge) av = __ldg(reinterpret_cast<const T*>(I.aval) + e);
             }
             int tot;
-            const int ex = Team<NT>::scan_excl(len, &tot, scratch);
+            const int ex = team_scan1<NT>(len, &tot, (calls++ & 1) ? scratch2 : scratch);
             const int idx = nA + (e - e0);
             if (valid && idx < MAXA) {
                 m_pre[idx] = u + ex;
@@ -282,9 +314,9 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
     }
     int nA, u;
     if (STAGED && small)
-        team_meta<NT, T, kStageMaxA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, nA, u);
+        team_meta<NT, T, kStageMaxA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, ctl + L::c_scan2, nA, u);
     else
-        team_meta<NT, T, L::MAXA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, nA, u);
+        team_meta<NT, T, L::MAXA>(a, ib, icount, rho, m_pre, m_bs, m_a, m_inst, ctl, ctl + L::c_scan2, nA, u);
     if (STAGED && small && nA > kStageMaxA) {  // the inputs changed under us
         if (tid == 0) atomicOr(a.status, kStatusInternal);
         __syncthreads();
@@ -347,7 +379,7 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
         const int vspan = ((int)sizeof(T) * u + 48 * nA + 15 + 15) & ~15;
         staged = __syncthreads_and(ok) && cspan + vspan <= L::stage_bytes;
         int total = 0;
-        if (staged) Team<NT>::scan_excl((int)(cbytes + vbytes), &total, ctl);
+        if (staged) team_scan1<NT>((int)(cbytes + vbytes), &total, ctl);
         staged = staged && total > 0;
         if (staged) {
             char* stage = sm + L::ocol;
@@ -433,7 +465,7 @@ __device__ __forceinline__ void num_row_team(const RowArgs& a, int unit, char* s
             }
         }
         int tot;
-        unsigned ex = (unsigned)Team<NT>::scan_excl(loc, &tot, ctl);
+        unsigned ex = (unsigned)team_scan1<NT>(loc, &tot, ctl + L::c_scan2);
         if (mine) {
             if (per >= 8) {
                 for (int i = 0; i < per; i += 8) {
@@ -586,14 +618,16 @@ __global__ void __launch_bounds__(32 * NW, (32 / NW) < 1 ? 1 : (32 / NW)) k_num_
         if (threadIdx.x == 0) mbar_init(reinterpret_cast<unsigned long long*>(smem + L::s_bar), 1);
         __syncthreads();
     }
-    // rows by ticket; the next ticket is drawn while the current row runs
+    // rows by ticket; the next ticket is drawn while the current row runs,
+    // into the other of two slots (the row's barriers publish it)
+    int slot = 0;
     if (threadIdx.x == 0) ctl[L::c_ticket] = atomicAdd(a.tick + a.bin, 1);
     __syncthreads();
     for (;;) {
-        const int i = begin + ctl[L::c_ticket];
+        const int i = begin + ctl[L::c_ticket + 2 * slot];
         if (i >= end) break;  // the same in every thread
-        __syncthreads();      // everyone has read the ticket
-        if (threadIdx.x == 0) ctl[L::c_ticket] = atomicAdd(a.tick + a.bin, 1);
+        if (threadIdx.x == 0) ctl[L::c_ticket + 2 * (slot ^ 1)] = atomicAdd(a.tick + a.bin, 1);
+        slot ^= 1;
         num_row_team<NW, T, STAGED>(a, __ldg(a.list + i), smem, &parity);  // ends with a block barrier
     }
 }
