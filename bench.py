@@ -561,6 +561,14 @@ def bench_trident(tsg, steps):
     out_bytes = sum(csr_bytes(C.nrows, C.nnz) for C in fp.C)
     out["roofline"] = workload_roofline(in_bytes + out_bytes, t_replay,
                                         "fused plan replay (k_num_rows per bin, one CUDA graph)")
+    # the per-bin autotuner on the same plan
+    tuned = fp.autotune()
+    fp.execute(True)
+    t_tuned = _time(lambda: fp.execute(True), steps)
+    out["batched_graph_autotuned_ms"] = round(t_tuned, 3)
+    out["autotune"] = {"num_bins": tuned.num_bins, "bin_upper": list(tuned.bin_upper)[:tuned.num_bins],
+                       "bin_kernel": list(tuned.bin_kernel)[:tuned.num_bins],
+                       "warps_per_block": tuned.warps_per_block}
     # fused, fresh: sizing + numeric every step
     fresh = lambda: tsg.Plan(plan.As, plan.Bs, plan.group_ptr).execute(False)
     t_fresh = _time(fresh, max(1, steps // 4))
