@@ -565,6 +565,7 @@ __device__ __forceinline__ void gather_strided(const RowArgs& a, int ib, int nA,
 // bitmap's storage while the products are gathered.
 
 constexpr int kSymBitsMax = 32768;
+constexpr int kSymMaxFlagged = 32;  // more flagged products in a row: count with a hash set
 
 template <int CAP>
 struct WSymLayout {
@@ -585,6 +586,7 @@ template <int PER>
 __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* sm) {
     constexpr int CAP = 32 * PER;
     using L = WSymLayout<CAP>;
+    static_assert(L::BITS >= 64 * pow2floor_c(2 * CAP - 1), "the fallback hash set needs 2 slots per product");
     unsigned* bm = reinterpret_cast<unsigned*>(sm + L::bm);
     int* m_pre = reinterpret_cast<int*>(sm + L::m_pre);
     int* m_bs = reinterpret_cast<int*>(sm + L::m_bs);
@@ -633,6 +635,47 @@ __device__ __forceinline__ void sym_row_warp(const RowArgs& a, int unit, char* s
             const unsigned bit = 1u << (h & 31);
             if (atomicOr(bm + (h >> 5), bit) & bit) flagged |= 1u << s;
         }
+    // A row that repeats its columns heavily flags most of its products; past
+    // kSymMaxFlagged the warp counts the distinct columns with a hash set
+    // instead (linear probing over 2 pow2ceil(u) slots, in the bitmap's
+    // storage: 64 bits per product leave room for two 32-bit slots).
+    int nflag = __popc(flagged);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nflag += __shfl_xor_sync(0xffffffffu, nflag, o);
+    if (nflag > kSymMaxFlagged) {
+        int* table = reinterpret_cast<int*>(bm);
+        const int T2 = 2 * pow2ceil(u);
+        const int tshift = 32 - (31 - __clz(T2));
+        __syncwarp();
+        for (int i = lane; i < T2; i += 32) table[i] = -1;
+        __syncwarp();
+        int fresh = 0;
+        bool overflow = false;
+#pragma unroll
+        for (int s = 0; s < PER; ++s) {
+            const int c = col[s];
+            if (c >= 0) {
+                unsigned h = ((unsigned)c * 0x9E3779B1u) >> tshift;
+                int probe = 0;
+                for (; probe < T2; ++probe) {
+                    const int old = atomicCAS(&table[h], -1, c);
+                    if (old == -1) {
+                        ++fresh;
+                        break;
+                    }
+                    if (old == c) break;
+                    h = (h + 1) & (unsigned)(T2 - 1);
+                }
+                overflow |= probe == T2;
+            }
+        }
+        if (overflow) atomicOr(a.status, kStatusHashOverflow);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+        if (lane == 0) a.counts[unit] = fresh;
+        __syncwarp();
+        return;
+    }
     // each flagged product against every product of the row (index s * 32 + lane)
     int dup = 0;
 #pragma unroll
