@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-extras", dest="extras", action="store_false")
     p.add_argument("--only", default=None,
                    help="run one further workload alone (e.g. many_products, trident_grid) and print its entry")
+    p.add_argument("--trident-n-log2", type=int, default=21,
+                   help="n = 2^L of the trident-grid workload (smaller for profiling)")
     p.add_argument("--many-count", type=int, default=256,
                    help="products of the many_products workload (the first N of the 256; smaller for profiling)")
     return p.parse_args()
@@ -470,30 +472,21 @@ def combine_over_ranks(ms: float, units: float, device: str = "cpu"):
 
 
 def e2e_public_api(tsg, A, B, prods, args):
-    """Same metric through the public API with host inputs: pinned host A, B
-    copied in, C = A B, C copied back to pinned host memory, every step."""
+    """Same metric through the public API with host inputs and output:
+    ``spgemm_host`` on page-locked A, B, every step copying both in, sizing,
+    computing C in row panels and copying each panel of C back to pinned
+    host memory while the next panels run.  The same product through the
+    device API with the copies issued one after another is reported beside
+    it (``serial_ms_per_step``)."""
     import torch
-    hostA = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-             for k, v in (("rp", A.rowptr.astype(np.int32)), ("col", A.col), ("val", A.val))}
-    hostB = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-             for k, v in (("rp", B.rowptr.astype(np.int32)), ("col", B.col), ("val", B.val))}
+    hA = tsg.DeviceCSR.from_host(A, device="cpu", pin=True)
+    hB = tsg.DeviceCSR.from_host(B, device="cpu", pin=True)
     h = tsg.Handle()
-    out = {}
+    box = {}
 
     def step():
-        dA = tsg.DeviceCSR(A.nrows, A.ncols, hostA["rp"].to("cuda", non_blocking=True),
-                           hostA["col"].to("cuda", non_blocking=True), hostA["val"].to("cuda", non_blocking=True))
-        dB = tsg.DeviceCSR(B.nrows, B.ncols, hostB["rp"].to("cuda", non_blocking=True),
-                           hostB["col"].to("cuda", non_blocking=True), hostB["val"].to("cuda", non_blocking=True))
-        C = tsg.spgemm(dA, dB, h)
-        if "col" not in out or out["col"].numel() != C.nnz:
-            out["rp"] = torch.empty(C.nrows + 1, dtype=torch.int32).pin_memory()
-            out["col"] = torch.empty(C.nnz, dtype=torch.int32).pin_memory()
-            out["val"] = torch.empty(C.nnz, dtype=torch.float64).pin_memory()
-        out["rp"].copy_(C.row_ptr, non_blocking=True)
-        out["col"].copy_(C.col, non_blocking=True)
-        out["val"].copy_(C.val, non_blocking=True)
-        return C.nnz
+        box["C"] = tsg.spgemm_host(hA, hB, h, panels=8, out=box.get("C"))
+        return box["C"].nnz
 
     nnz = step()
     torch.cuda.synchronize()
@@ -503,11 +496,32 @@ def e2e_public_api(tsg, A, B, prods, args):
         step()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    h2d = sum(int(v.numel() * v.element_size()) for v in list(hostA.values()) + list(hostB.values()))
+    out = {}
+
+    def serial():
+        dA = tsg.DeviceCSR(A.nrows, A.ncols, hA.row_ptr.to("cuda", non_blocking=True),
+                           hA.col.to("cuda", non_blocking=True), hA.val.to("cuda", non_blocking=True))
+        dB = tsg.DeviceCSR(B.nrows, B.ncols, hB.row_ptr.to("cuda", non_blocking=True),
+                           hB.col.to("cuda", non_blocking=True), hB.val.to("cuda", non_blocking=True))
+        C = tsg.spgemm(dA, dB, h)
+        C2 = box["C"]
+        C2.row_ptr.copy_(C.row_ptr, non_blocking=True)
+        C2.col.copy_(C.col, non_blocking=True)
+        C2.val.copy_(C.val, non_blocking=True)
+
+    serial()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        serial()
+    torch.cuda.synchronize()
+    dts = (time.perf_counter() - t0) / steps
+    h2d = sum(int(t.numel() * t.element_size()) for t in (hA.row_ptr, hA.col, hA.val, hB.row_ptr, hB.col, hB.val))
     d2h = (A.nrows + 1) * 4 + nnz * 12
     h.close()
     return {"value": round(2 * prods / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3), "steps": steps}
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3), "steps": steps,
+            "api": "spgemm_host (8 row panels, copies overlapped)", "serial_ms_per_step": round(dts * 1e3, 3)}
 
 
 def _time(fn, steps, warmup=1, stream=None):
@@ -526,12 +540,13 @@ def _time(fn, steps, warmup=1, stream=None):
     return e0.elapsed_time(e1) / steps
 
 
-def bench_trident(tsg, steps):
+def bench_trident(tsg, steps, n_log2=21):
     """ER A, B with n = 2^21 and 32 per row, float64, on the trident grid
-    4 x 4 x lambda=4: 256 block products, 64 output blocks of 4 rounds."""
+    4 x 4 x lambda=4: 256 block products, 64 output blocks of 4 rounds
+    (n_log2 < 21: a smaller grid of the same shape, for profiling)."""
     import torch
     import gen
-    n, d, q, lam = 1 << 21, 32, 4, 4
+    n, d, q, lam = 1 << n_log2, 32, 4, 4
     A = gen.er(n, n, d, 4)
     B = gen.er(n, n, d, 5)
     prods = products(A, B)
@@ -540,7 +555,7 @@ def bench_trident(tsg, steps):
     h = tsg.Handle()
     t_split = _time(lambda: tsg.TridentPlan(dA, dB, q, lam, h), 1, warmup=1)
     plan = tsg.TridentPlan(dA, dB, q, lam, h)
-    out = {"workload": "ER A*B n=2^21 d=32 f64, trident 4x4x4 (256 block products, 64 blocks)",
+    out = {"workload": f"ER A*B n=2^{n_log2} d=32 f64, trident 4x4x4 (256 block products, 64 blocks)",
            "products": prods, "partition_ms": round(t_split, 3)}
     # fused, persistent: sized once, numeric replayed from a CUDA graph
     fp = plan.fused_plan()
@@ -860,7 +875,12 @@ def run_only(args):
     __graft_entry__.build()
     import paper_2603_21444_gb300 as tsg
     fn = extra_fn(args.only)
-    res = fn(tsg, args.steps, args.many_count) if args.only == "many_products" else fn(tsg, args.steps)
+    if args.only == "many_products":
+        res = fn(tsg, args.steps, args.many_count)
+    elif args.only == "trident_grid":
+        res = fn(tsg, args.steps, args.trident_n_log2)
+    else:
+        res = fn(tsg, args.steps)
     print(json.dumps({"workload_only": args.only, args.only: res}), flush=True)
 
 

@@ -197,6 +197,34 @@ spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const sp
 spgemm_status spgemm_fused(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A, const spgemm_csr_in* B,
                            spgemm_csr_out* C, int64_t capacity, int64_t* c_nnz, spgemm_stream_t stream);
 
+/* ------------------------------------------- product from host memory
+ *
+ * The same product as spgemm_symbolic + spgemm_numeric (Sec. 2), for inputs
+ * and outputs in host memory, with the transfers overlapped: the output
+ * rows are computed in `panels` row panels, and each panel's columns and
+ * values travel to the host on a second stream of the handle while the
+ * next panels are computed.  Host arrays in page-locked memory get the full
+ * link bandwidth (pageable memory works, at the driver's staging speed).
+ *
+ * spgemm_host_symbolic: A, B are host CSR arrays (row_ptr, col_idx; val may
+ *   be NULL); copies them into device buffers the handle owns (grown on
+ *   demand, kept), sizes C and writes its row_ptr to c_row_ptr (host,
+ *   A.nrows + 1 entries) and its nnz to *c_nnz.  Synchronises.
+ * spgemm_host_numeric: A, B the same host arrays, now with values of
+ *   `dtype`; C->row_ptr the host row_ptr from the sizing call, C->col_idx
+ *   and C->val host arrays of *c_nnz entries.  A call right after the sizing
+ *   call with the same A and B pointers reuses the device copies of the
+ *   indices and copies the values only; the host arrays must not change in
+ *   between.  panels: 1..1024 (0 = 8).  Synchronises before returning.
+ * Errors as the device calls; SPGEMM_ERR_OOM when the handle's buffers
+ * cannot grow.
+ */
+spgemm_status spgemm_host_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                   int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream);
+spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
+                                  const spgemm_csr_in* B, spgemm_csr_out* C, int32_t panels,
+                                  spgemm_stream_t stream);
+
 /* ------------------------------------ ordered sum of partials (Sec. 4.4, Alg. 1)
  *
  * spgemm_merge: C = parts[0] + parts[1] + ... + parts[nparts-1] for CSR

@@ -64,6 +64,12 @@ struct spgemm_handle {
     DevBuf mcl;     // Markov clustering: bounds, offsets, kept entries
     DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
     DevBuf perm;    // permutation: target hits, row lengths, scan, long-row list, ranks
+    DevBuf hx;      // product from host memory: device copies of A, B and C's row_ptr
+    DevBuf hc;      // ... and of C's columns and values
+    const void* hx_key[4] = {};  // host A.row_ptr, A.col, B.row_ptr, B.col of the last sizing call
+    bool hx_sized = false;
+    cudaStream_t copy = nullptr;  // device-to-host copies of finished row panels
+    std::vector<cudaEvent_t> panel_ev;
     int mcl_n = -1;
     long long mcl_acc_key = -1;  // accumulator layout (stride, slots) whose arrays are known to be zero
     long long mcl_total = 0;
@@ -121,7 +127,8 @@ spgemm_status cuda_status(cudaError_t e) {
 
 // Device bytes the handle's workspace buffers hold.
 size_t held_bytes(const spgemm_handle* h) {
-    return h->units.n + h->small.n + h->dense.n + h->status.n + h->tr.n + h->mcl.n + h->mcl_acc.n + h->perm.n;
+    return h->units.n + h->small.n + h->dense.n + h->status.n + h->tr.n + h->mcl.n + h->mcl_acc.n + h->perm.n +
+           h->hx.n + h->hc.n;
 }
 
 // Grows b (one of h's buffers, or a buffer that will replace one) to at
@@ -671,6 +678,39 @@ bool csr_in_ok(const spgemm_csr_in* X, bool need_val) {
 
 }  // namespace
 
+namespace {
+
+// Offsets of the device copies in h->hx: A row_ptr | A col | A val | B row_ptr
+// | B col | B val | C row_ptr (values sized for 8 bytes).
+struct HostLayout {
+    size_t arp, acol, aval, brp, bcol, bval, crp, bytes;
+    HostLayout(const spgemm_csr_in* A, const spgemm_csr_in* B) {
+        arp = 0;
+        acol = arp + align16(4 * ((size_t)A->nrows + 1));
+        aval = acol + align16(4 * (size_t)A->nnz);
+        brp = aval + align16(8 * (size_t)A->nnz);
+        bcol = brp + align16(4 * ((size_t)B->nrows + 1));
+        bval = bcol + align16(4 * (size_t)B->nnz);
+        crp = bval + align16(8 * (size_t)B->nnz);
+        bytes = crp + align16(4 * ((size_t)A->nrows + 1));
+    }
+};
+
+bool host_in_ok(const spgemm_csr_in* X, bool need_val) {
+    if (!csr_in_ok(X, false)) return false;
+    return !(need_val && X->nnz > 0 && !X->val);
+}
+
+spgemm_csr_in dev_view(const spgemm_csr_in* X, char* base, size_t rp, size_t col, size_t val, bool vals) {
+    spgemm_csr_in d = *X;
+    d.row_ptr = reinterpret_cast<const int32_t*>(base + rp);
+    d.col_idx = reinterpret_cast<const int32_t*>(base + col);
+    d.val = vals ? static_cast<const void*>(base + val) : nullptr;
+    return d;
+}
+
+}  // namespace
+
 // ====================================================================== ABI
 
 extern "C" {
@@ -748,6 +788,13 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->mcl.p) cudaFree(h->mcl.p);
     if (h->mcl_acc.p) cudaFree(h->mcl_acc.p);
     if (h->perm.p) cudaFree(h->perm.p);
+    if (h->hx.p) cudaFree(h->hx.p);
+    if (h->hc.p) cudaFree(h->hc.p);
+    if (h->copy) {
+        cudaStreamSynchronize(h->copy);
+        cudaStreamDestroy(h->copy);
+    }
+    for (cudaEvent_t e : h->panel_ev) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -792,6 +839,99 @@ spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_
                                  {B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz}};
     return run(h, dtype, false, inst, groups, false, nullptr, h->tune, checks,
                reinterpret_cast<cudaStream_t>(stream));
+}
+
+spgemm_status spgemm_host_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B,
+                                   int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream) {
+    if (!h || !host_in_ok(A, false) || !host_in_ok(B, false) || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+    if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    h->hx_sized = false;
+    const HostLayout L(A, B);
+    TSG_TRY(grow(h, h->hx, L.bytes));
+    char* x = static_cast<char*>(h->hx.p);
+    TSG_CHECK(cudaMemcpyAsync(x + L.arp, A->row_ptr, 4 * ((size_t)A->nrows + 1), cudaMemcpyHostToDevice, st));
+    if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.acol, A->col_idx, 4 * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
+    TSG_CHECK(cudaMemcpyAsync(x + L.brp, B->row_ptr, 4 * ((size_t)B->nrows + 1), cudaMemcpyHostToDevice, st));
+    if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bcol, B->col_idx, 4 * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
+    const spgemm_csr_in dA = dev_view(A, x, L.arp, L.acol, L.aval, false);
+    const spgemm_csr_in dB = dev_view(B, x, L.brp, L.bcol, L.bval, false);
+    TSG_TRY(spgemm_symbolic(h, &dA, &dB, reinterpret_cast<int32_t*>(x + L.crp), c_nnz, stream));
+    TSG_CHECK(cudaMemcpyAsync(c_row_ptr, x + L.crp, 4 * ((size_t)A->nrows + 1), cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(cudaStreamSynchronize(st));
+    h->hx_key[0] = A->row_ptr;
+    h->hx_key[1] = A->col_idx;
+    h->hx_key[2] = B->row_ptr;
+    h->hx_key[3] = B->col_idx;
+    h->hx_sized = true;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
+                                  const spgemm_csr_in* B, spgemm_csr_out* C, int32_t panels,
+                                  spgemm_stream_t stream) {
+    if (!h || !host_in_ok(A, true) || !host_in_ok(B, true) || !C || !C->row_ptr) return SPGEMM_ERR_INVALID_ARG;
+    if (dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
+    if (A->ncols != B->nrows || C->nrows != A->nrows || C->ncols != B->ncols) return SPGEMM_ERR_SHAPE;
+    if (panels < 0 || panels > 1024) return SPGEMM_ERR_INVALID_ARG;
+    if (panels == 0) panels = 8;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int m = A->nrows;
+    const long long nnz = C->row_ptr[m];
+    if (nnz < 0 || nnz > 2147483647ll) return SPGEMM_ERR_INVALID_ARG;
+    if (nnz > 0 && (!C->col_idx || !C->val)) return SPGEMM_ERR_INVALID_ARG;
+    const size_t esz = dtype == SPGEMM_F64 ? 8 : 4;
+    const HostLayout L(A, B);
+    const bool same = h->hx_sized && h->hx.n >= L.bytes && h->hx_key[0] == A->row_ptr &&
+                      h->hx_key[1] == A->col_idx && h->hx_key[2] == B->row_ptr && h->hx_key[3] == B->col_idx;
+    h->hx_sized = false;
+    if (!same) TSG_TRY(grow(h, h->hx, L.bytes));
+    TSG_TRY(grow(h, h->hc, align16(4 * (size_t)nnz) + esz * (size_t)nnz));
+    char* x = static_cast<char*>(h->hx.p);
+    int32_t* ccol = static_cast<int32_t*>(h->hc.p);
+    char* cval = static_cast<char*>(h->hc.p) + align16(4 * (size_t)nnz);
+    if (!same) {
+        // not the sizing call's inputs: indices and C's row_ptr again
+        TSG_CHECK(cudaMemcpyAsync(x + L.arp, A->row_ptr, 4 * ((size_t)m + 1), cudaMemcpyHostToDevice, st));
+        if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.acol, A->col_idx, 4 * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
+        TSG_CHECK(cudaMemcpyAsync(x + L.brp, B->row_ptr, 4 * ((size_t)B->nrows + 1), cudaMemcpyHostToDevice, st));
+        if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bcol, B->col_idx, 4 * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
+        TSG_CHECK(cudaMemcpyAsync(x + L.crp, C->row_ptr, 4 * ((size_t)m + 1), cudaMemcpyHostToDevice, st));
+    }
+    if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.aval, A->val, esz * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
+    if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bval, B->val, esz * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
+    if (!h->copy) TSG_CHECK(cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
+    while ((int)h->panel_ev.size() < panels) {
+        cudaEvent_t e;
+        TSG_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->panel_ev.push_back(e);
+    }
+    const spgemm_csr_in dB = dev_view(B, x, L.brp, L.bcol, L.bval, true);
+    spgemm_status rc = SPGEMM_OK;
+    for (int p = 0; p < panels && rc == SPGEMM_OK; ++p) {
+        const int r0 = (int)((long long)p * m / panels), r1 = (int)((long long)(p + 1) * m / panels);
+        if (r1 <= r0) continue;
+        // rows [r0, r1): row pointers are absolute offsets into the full arrays
+        spgemm_csr_in dA = dev_view(A, x, L.arp, L.acol, L.aval, true);
+        dA.nrows = r1 - r0;
+        dA.row_ptr += r0;
+        spgemm_csr_out dC{r1 - r0, C->ncols, reinterpret_cast<int32_t*>(x + L.crp) + r0, ccol, cval};
+        rc = spgemm_numeric(h, dtype, &dA, &dB, &dC, stream);
+        if (rc != SPGEMM_OK) break;
+        const long long e0 = C->row_ptr[r0], e1 = C->row_ptr[r1];
+        if (e1 <= e0) continue;
+        TSG_CHECK(cudaEventRecord(h->panel_ev[p], st));
+        TSG_CHECK(cudaStreamWaitEvent(h->copy, h->panel_ev[p], 0));
+        TSG_CHECK(cudaMemcpyAsync(C->col_idx + e0, ccol + e0, 4 * (size_t)(e1 - e0), cudaMemcpyDeviceToHost, h->copy));
+        TSG_CHECK(cudaMemcpyAsync(static_cast<char*>(C->val) + esz * e0, cval + esz * e0, esz * (size_t)(e1 - e0),
+                                  cudaMemcpyDeviceToHost, h->copy));
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(h->copy);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc != SPGEMM_OK) return rc;
+    TSG_CHECK(e1);
+    TSG_CHECK(e2);
+    return spgemm_device_status(h);
 }
 
 spgemm_status spgemm_products(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B, int64_t* total,
