@@ -209,18 +209,27 @@ spgemm_status spgemm_fused(spgemm_handle* h, spgemm_dtype dtype, const spgemm_cs
  * spgemm_host_symbolic: A, B are host CSR arrays (row_ptr, col_idx; val may
  *   be NULL); copies them into device buffers the handle owns (grown on
  *   demand, kept), sizes C and writes its row_ptr to c_row_ptr (host,
- *   A.nrows + 1 entries) and its nnz to *c_nnz.  Synchronises.
+ *   A.nrows + 1 entries) and its nnz to *c_nnz.  Synchronises on `stream`.
+ *   value_dtype: SPGEMM_F32 / SPGEMM_F64 when A->val and B->val hold values
+ *   of that type: their upload starts on the handle's second stream and runs
+ *   while the sizing does (it may still be running when the call returns);
+ *   -1: the values are not touched.
  * spgemm_host_numeric: A, B the same host arrays, now with values of
  *   `dtype`; C->row_ptr the host row_ptr from the sizing call, C->col_idx
  *   and C->val host arrays of *c_nnz entries.  A call right after the sizing
  *   call with the same A and B pointers reuses the device copies of the
- *   indices and copies the values only; the host arrays must not change in
- *   between.  panels: 1..1024 (0 = 8).  Synchronises before returning.
+ *   indices (and of the values, when the sizing call uploaded them with this
+ *   dtype); the host arrays must not change in between.  A later call with
+ *   the same pointers copies everything again.  C is computed in `panels`
+ *   row panels (1..1024, 0 = 8; the first half the size of the others); the
+ *   columns and values of each finished panel are copied out while the next
+ *   ones run.  Synchronises before returning.
  * Errors as the device calls; SPGEMM_ERR_OOM when the handle's buffers
  * cannot grow.
  */
-spgemm_status spgemm_host_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B,
-                                   int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream);
+spgemm_status spgemm_host_symbolic(spgemm_handle* h, int32_t value_dtype, const spgemm_csr_in* A,
+                                   const spgemm_csr_in* B, int32_t* c_row_ptr, int64_t* c_nnz,
+                                   spgemm_stream_t stream);
 spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_csr_in* A,
                                   const spgemm_csr_in* B, spgemm_csr_out* C, int32_t panels,
                                   spgemm_stream_t stream);

@@ -68,7 +68,8 @@ SIGNATURES = {
     "spgemm_symbolic": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, I64P, P], ctypes.c_int),
     "spgemm_numeric": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P],
                        ctypes.c_int),
-    "spgemm_host_symbolic": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, I64P, P], ctypes.c_int),
+    "spgemm_host_symbolic": ([P, ctypes.c_int32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), P, I64P, P],
+                             ctypes.c_int),
     "spgemm_host_numeric": ([P, ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut),
                              I32, P], ctypes.c_int),
     "spgemm_merge": ([P, ctypes.c_int, I32, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), I64P, P], ctypes.c_int),

@@ -245,8 +245,9 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, stream=None
 def spgemm_host(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, panels: int = 8, out: DeviceCSR | None = None,
                 stream=None) -> DeviceCSR:
     """C = A B with A, B and C in host memory (``spgemm_host_symbolic`` +
-    ``spgemm_host_numeric``: the library copies the inputs in, computes C in
-    row panels and copies each panel out while the next ones run).  A and B
+    ``spgemm_host_numeric``: the library copies the inputs in (the values
+    while the sizing runs), computes C in row panels and copies each panel
+    out while the next ones run).  A and B
     are DeviceCSR containers of CPU tensors, page-locked for full speed
     (``DeviceCSR.from_host(x, device="cpu", pin=True)``); ``out``, when its
     sizes match, receives C (pinned buffers reused across calls)."""
@@ -257,8 +258,9 @@ def spgemm_host(A: DeviceCSR, B: DeviceCSR, handle: Handle | None = None, panels
     rp = out.row_ptr if out is not None and out.row_ptr.numel() == A.nrows + 1 else \
         torch.empty(A.nrows + 1, dtype=torch.int32).pin_memory()
     nnz = ctypes.c_int64()
-    check(_abi.lib().spgemm_host_symbolic(h.ptr, ctypes.byref(ain), ctypes.byref(bin_), ctypes.c_void_p(rp.data_ptr()),
-                                          ctypes.byref(nnz), _stream(stream)), "spgemm_host_symbolic")
+    check(_abi.lib().spgemm_host_symbolic(h.ptr, _dtype_code(A.val.dtype), ctypes.byref(ain), ctypes.byref(bin_),
+                                          ctypes.c_void_p(rp.data_ptr()), ctypes.byref(nnz), _stream(stream)),
+          "spgemm_host_symbolic")
     n = int(nnz.value)
     if out is not None and out.col.numel() == n and out.val is not None and out.val.dtype == A.val.dtype:
         col, val = out.col, out.val

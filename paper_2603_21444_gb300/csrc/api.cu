@@ -68,12 +68,17 @@ struct spgemm_handle {
     DevBuf hc;      // ... and of C's columns and values
     const void* hx_key[4] = {};  // host A.row_ptr, A.col, B.row_ptr, B.col of the last sizing call
     bool hx_sized = false;
-    cudaStream_t copy = nullptr;  // device-to-host copies of finished row panels
+    const void* hv_key[2] = {};  // host A.val, B.val whose copies the last sizing call started
+    int hv_dtype = -1;
+    bool hv_ready = false;
+    cudaEvent_t hv_ev = nullptr;  // ... recorded on `copy` after them
+    cudaStream_t copy = nullptr;  // value uploads during the sizing; copies of finished row panels out
     std::vector<cudaEvent_t> panel_ev;
     int mcl_n = -1;
     long long mcl_acc_key = -1;  // accumulator layout (stride, slots) whose arrays are known to be zero
     long long mcl_total = 0;
-    void* pinned = nullptr;
+    void* pinned = nullptr;      // mapped page-locked words the kernels' small results are stored into
+    void* pinned_dev = nullptr;  // ... the device address of the same memory
     size_t pinned_n = 0;
     // plan cache (bin lists of the last sizing call)
     uint64_t plan_sig = 0;
@@ -160,14 +165,33 @@ spgemm_status grow_pinned(spgemm_handle* h, size_t bytes) {
     if (h->pinned_n >= bytes) return SPGEMM_OK;
     if (h->pinned) cudaFreeHost(h->pinned);
     h->pinned = nullptr;
+    h->pinned_dev = nullptr;
     h->pinned_n = 0;
     size_t n = std::max(bytes, size_t(4096));
-    if (cudaMallocHost(&h->pinned, n) != cudaSuccess) {
+    if (cudaHostAlloc(&h->pinned, n, cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
+        h->pinned = nullptr;
         return SPGEMM_ERR_OOM;
+    }
+    if (cudaHostGetDevicePointer(&h->pinned_dev, h->pinned, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h->pinned);
+        h->pinned = nullptr;
+        return SPGEMM_ERR_CUDA;
     }
     h->pinned_n = n;
     return SPGEMM_OK;
+}
+
+// Reads `bytes` of device memory into h->pinned at host address p (inside
+// h->pinned) with a kernel on st, so that the read never waits behind a
+// large copy-engine transfer of another stream; the caller synchronises st.
+cudaError_t readback(spgemm_handle* h, void* p, const void* d, size_t bytes, cudaStream_t st) {
+    const size_t off = static_cast<size_t>(static_cast<char*>(p) - static_cast<char*>(h->pinned));
+    if (!h->pinned || static_cast<char*>(p) < static_cast<char*>(h->pinned) || off + bytes > h->pinned_n)
+        return cudaErrorInvalidValue;
+    ++h->launches;
+    return launch_readback(static_cast<char*>(h->pinned_dev) + off, d, bytes, st);
 }
 
 void default_tune(spgemm_tune* t) {
@@ -461,7 +485,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             TSG_CHECK(launch_validate(v.rp, v.col, v.nrows, v.ncols, v.nnz, d_status, st));
             ++h->launches;
         }
-        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_status, d_status, 4, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         if (*p_status & kStatusNotCanonical) {
             h->plan_valid = false;
@@ -517,7 +541,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     const int chunk = heavy_chunk_for(max_ncols);
 
     if (products_only) {
-        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_nnz, d_nnz, 8, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         *c_nnz = p_nnz[0];
         return SPGEMM_OK;
@@ -525,7 +549,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     if (fused_cap >= 0) {
         // single pass: all rows must sit in warp-team bins of increasing capacity
         h->plan_valid = false;
-        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_hist, d_hist, 4 * nslots, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         if (ngroups != 1 || p_hist[nb] > 0) return SPGEMM_ERR_UNSUPPORTED;
         int bmax = -1;
@@ -557,8 +581,8 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             ++h->launches;
         }
         int* p_total = reinterpret_cast<int*>(p_nnz);
-        TSG_CHECK(cudaMemcpyAsync(p_total, groups[0].crp + U, 4, cudaMemcpyDeviceToHost, st));
-        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_total, groups[0].crp + U, 4, st));
+        TSG_CHECK(readback(h, p_status, d_status, 4, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         const unsigned status = *p_status;
         if (status) TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
@@ -591,9 +615,9 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
             TSG_CHECK(launch_rowptr(d_groups, d_ubase, ngroups, U, d_ex, d_nnz, st));
             h->launches += 4;
         }
-        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8 * ngroups, cudaMemcpyDeviceToHost, st));
-        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
-        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_nnz, d_nnz, 8 * ngroups, st));
+        TSG_CHECK(readback(h, p_hist, d_hist, 4 * nslots, st));
+        TSG_CHECK(readback(h, p_status, d_status, 4, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         const unsigned status = *p_status;
         // a latched error (this call's or an earlier asynchronous call's) is
@@ -619,7 +643,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
     if (reuse) {
         hist = h->plan_hist;
     } else {
-        TSG_CHECK(cudaMemcpyAsync(p_hist, d_hist, 4 * nslots, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_hist, d_hist, 4 * nslots, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         hist.assign(p_hist, p_hist + nslots);
     }
@@ -660,7 +684,7 @@ spgemm_status run(spgemm_handle* h, int dtype, bool merge, const std::vector<Ins
         la.glist = nullptr;
     }
     if (tune.validate) {
-        TSG_CHECK(cudaMemcpyAsync(p_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_status, d_status, 4, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         const unsigned status = *p_status;
         if (status) TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
@@ -795,6 +819,7 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
         cudaStreamDestroy(h->copy);
     }
     for (cudaEvent_t e : h->panel_ev) cudaEventDestroy(e);
+    if (h->hv_ev) cudaEventDestroy(h->hv_ev);
     if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return SPGEMM_OK;
@@ -841,15 +866,31 @@ spgemm_status spgemm_numeric(spgemm_handle* h, spgemm_dtype dtype, const spgemm_
                reinterpret_cast<cudaStream_t>(stream));
 }
 
-spgemm_status spgemm_host_symbolic(spgemm_handle* h, const spgemm_csr_in* A, const spgemm_csr_in* B,
-                                   int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream) {
+spgemm_status spgemm_host_symbolic(spgemm_handle* h, int32_t value_dtype, const spgemm_csr_in* A,
+                                   const spgemm_csr_in* B, int32_t* c_row_ptr, int64_t* c_nnz,
+                                   spgemm_stream_t stream) {
     if (!h || !host_in_ok(A, false) || !host_in_ok(B, false) || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+    if (value_dtype != -1 && value_dtype != SPGEMM_F32 && value_dtype != SPGEMM_F64) return SPGEMM_ERR_DTYPE;
     if (A->ncols != B->nrows) return SPGEMM_ERR_SHAPE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     h->hx_sized = false;
+    h->hv_ready = false;
+    // an earlier call's uploads into the buffers must be over before they move
+    if (h->copy) TSG_CHECK(cudaStreamSynchronize(h->copy));
     const HostLayout L(A, B);
     TSG_TRY(grow(h, h->hx, L.bytes));
     char* x = static_cast<char*>(h->hx.p);
+    const bool vals = value_dtype != -1 && (A->nnz == 0 || A->val) && (B->nnz == 0 || B->val);
+    if (vals) {
+        // the values are not needed for the sizing: their upload runs on the
+        // second stream meanwhile, and the numeric call waits for it
+        const size_t esz = value_dtype == SPGEMM_F64 ? 8 : 4;
+        if (!h->copy) TSG_CHECK(cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
+        if (!h->hv_ev) TSG_CHECK(cudaEventCreateWithFlags(&h->hv_ev, cudaEventDisableTiming));
+        if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bval, B->val, esz * (size_t)B->nnz, cudaMemcpyHostToDevice, h->copy));
+        if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.aval, A->val, esz * (size_t)A->nnz, cudaMemcpyHostToDevice, h->copy));
+        TSG_CHECK(cudaEventRecord(h->hv_ev, h->copy));
+    }
     TSG_CHECK(cudaMemcpyAsync(x + L.arp, A->row_ptr, 4 * ((size_t)A->nrows + 1), cudaMemcpyHostToDevice, st));
     if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.acol, A->col_idx, 4 * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
     TSG_CHECK(cudaMemcpyAsync(x + L.brp, B->row_ptr, 4 * ((size_t)B->nrows + 1), cudaMemcpyHostToDevice, st));
@@ -864,6 +905,12 @@ spgemm_status spgemm_host_symbolic(spgemm_handle* h, const spgemm_csr_in* A, con
     h->hx_key[2] = B->row_ptr;
     h->hx_key[3] = B->col_idx;
     h->hx_sized = true;
+    if (vals) {
+        h->hv_key[0] = A->val;
+        h->hv_key[1] = B->val;
+        h->hv_dtype = value_dtype;
+        h->hv_ready = true;
+    }
     return SPGEMM_OK;
 }
 
@@ -884,8 +931,14 @@ spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const sp
     const HostLayout L(A, B);
     const bool same = h->hx_sized && h->hx.n >= L.bytes && h->hx_key[0] == A->row_ptr &&
                       h->hx_key[1] == A->col_idx && h->hx_key[2] == B->row_ptr && h->hx_key[3] == B->col_idx;
+    const bool have_vals = same && h->hv_ready && h->hv_dtype == (int)dtype && h->hv_key[0] == A->val &&
+                           h->hv_key[1] == B->val;
     h->hx_sized = false;
-    if (!same) TSG_TRY(grow(h, h->hx, L.bytes));
+    h->hv_ready = false;
+    if (!same) {
+        if (h->copy) TSG_CHECK(cudaStreamSynchronize(h->copy));
+        TSG_TRY(grow(h, h->hx, L.bytes));
+    }
     TSG_TRY(grow(h, h->hc, align16(4 * (size_t)nnz) + esz * (size_t)nnz));
     char* x = static_cast<char*>(h->hx.p);
     int32_t* ccol = static_cast<int32_t*>(h->hc.p);
@@ -898,8 +951,12 @@ spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const sp
         if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bcol, B->col_idx, 4 * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
         TSG_CHECK(cudaMemcpyAsync(x + L.crp, C->row_ptr, 4 * ((size_t)m + 1), cudaMemcpyHostToDevice, st));
     }
-    if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.aval, A->val, esz * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
-    if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bval, B->val, esz * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
+    if (have_vals) {
+        TSG_CHECK(cudaStreamWaitEvent(st, h->hv_ev, 0));  // uploaded during the sizing call
+    } else {
+        if (A->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.aval, A->val, esz * (size_t)A->nnz, cudaMemcpyHostToDevice, st));
+        if (B->nnz) TSG_CHECK(cudaMemcpyAsync(x + L.bval, B->val, esz * (size_t)B->nnz, cudaMemcpyHostToDevice, st));
+    }
     if (!h->copy) TSG_CHECK(cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
     while ((int)h->panel_ev.size() < panels) {
         cudaEvent_t e;
@@ -907,16 +964,42 @@ spgemm_status spgemm_host_numeric(spgemm_handle* h, spgemm_dtype dtype, const sp
         h->panel_ev.push_back(e);
     }
     const spgemm_csr_in dB = dev_view(B, x, L.brp, L.bcol, L.bval, true);
+    // A panel's row_ptr view starts at an absolute offset, which the input
+    // check would reject: the whole matrices are checked once (here, or by
+    // the sizing call on the same arrays) and the panels run unchecked.
+    spgemm_tune tp = h->tune;
+    if (tp.validate && !same) {
+        const spgemm_csr_in fA = dev_view(A, x, L.arp, L.acol, L.aval, false);
+        TSG_TRY(grow(h, h->status, 16, st, true));
+        TSG_TRY(grow_pinned(h, 16));
+        unsigned* d_status = static_cast<unsigned*>(h->status.p);
+        for (const spgemm_csr_in* X : {&fA, &dB}) {
+            TSG_CHECK(launch_validate(X->row_ptr, X->col_idx, X->nrows, X->ncols, (int)X->nnz, d_status, st));
+            ++h->launches;
+        }
+        TSG_CHECK(readback(h, h->pinned, d_status, 4, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        if (*static_cast<const unsigned*>(h->pinned) & kStatusNotCanonical) {
+            TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
+            return SPGEMM_ERR_NOT_CANONICAL;
+        }
+    }
+    tp.validate = 0;
     spgemm_status rc = SPGEMM_OK;
     for (int p = 0; p < panels && rc == SPGEMM_OK; ++p) {
-        const int r0 = (int)((long long)p * m / panels), r1 = (int)((long long)(p + 1) * m / panels);
+        // the first panel is half the others: the copies out start sooner
+        const long long den = 2ll * panels - 1;
+        const int r0 = p == 0 ? 0 : (int)((2ll * p - 1) * m / den);
+        const int r1 = (int)((2ll * p + 1) * m / den);
         if (r1 <= r0) continue;
         // rows [r0, r1): row pointers are absolute offsets into the full arrays
         spgemm_csr_in dA = dev_view(A, x, L.arp, L.acol, L.aval, true);
         dA.nrows = r1 - r0;
         dA.row_ptr += r0;
-        spgemm_csr_out dC{r1 - r0, C->ncols, reinterpret_cast<int32_t*>(x + L.crp) + r0, ccol, cval};
-        rc = spgemm_numeric(h, dtype, &dA, &dB, &dC, stream);
+        int32_t* crp = reinterpret_cast<int32_t*>(x + L.crp) + r0;
+        std::vector<InstDev> inst{{dA.row_ptr, dA.col_idx, dA.val, dB.row_ptr, dB.col_idx, dB.val, dB.nnz}};
+        std::vector<GroupDev> groups{{0, 1, dA.nrows, dB.ncols, crp, ccol, cval, 0}};
+        rc = run(h, dtype, false, inst, groups, false, nullptr, tp, {}, st);
         if (rc != SPGEMM_OK) break;
         const long long e0 = C->row_ptr[r0], e1 = C->row_ptr[r1];
         if (e1 <= e0) continue;
@@ -1119,7 +1202,7 @@ spgemm_status spgemm_tile_split(spgemm_handle* h, spgemm_dtype dtype, const spge
         h->launches += 5;
         TSG_TRY(grow_pinned(h, 8 * nt));
         long long* p_nnz = static_cast<long long*>(h->pinned);
-        TSG_CHECK(cudaMemcpyAsync(p_nnz, d_nnz, 8 * nt, cudaMemcpyDeviceToHost, st));
+        TSG_CHECK(readback(h, p_nnz, d_nnz, 8 * nt, st));
         TSG_CHECK(cudaStreamSynchronize(st));
         for (int cp = 0; cp < ncp; ++cp)
             for (int rp = 0; rp < nrp; ++rp) tile_nnz[rp * ncp + cp] = p_nnz[cp * nrp + rp];
@@ -1272,9 +1355,10 @@ spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spg
     p.sms = h->sms;
     TSG_CHECK(launch_permute(p, st));
     h->launches += (row_perm ? 2 : 0) + (col_perm ? 2 : 0) + 1 + 4 + 2;
-    unsigned status = 0;
+    TSG_TRY(grow_pinned(h, 16));
+    TSG_CHECK(readback(h, h->pinned, d_status, 4, st));
     TSG_CHECK(cudaStreamSynchronize(st));
-    TSG_CHECK(cudaMemcpy(&status, d_status, 4, cudaMemcpyDeviceToHost));
+    const unsigned status = *static_cast<const unsigned*>(h->pinned);
     if (status & kStatusBadMap) {
         TSG_CHECK(cudaMemsetAsync(d_status, 0, 4, st));
         return SPGEMM_ERR_INVALID_ARG;
@@ -1399,7 +1483,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     TSG_CHECK(launch_mcl_bounds(Mt->row_ptr, Mt->col_idx, (int)n, prm->topk, reinterpret_cast<int*>(b + L0.ub), st));
     TSG_CHECK(launch_scan(reinterpret_cast<int*>(b + L0.ub), n, reinterpret_cast<long long*>(b + L0.bsum),
                           reinterpret_cast<long long*>(b + L0.ub_off), st));
-    TSG_CHECK(cudaMemcpyAsync(p_ll, b + L0.ub_off + 8 * n, 8, cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(readback(h, p_ll, b + L0.ub_off + 8 * n, 8, st));
     TSG_CHECK(cudaStreamSynchronize(st));
     const long long total = p_ll[0];
     MclLayout L = mcl_layout(n, total);
@@ -1458,8 +1542,8 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     TSG_CHECK(launch_ll_to_int(reinterpret_cast<long long*>(b + L.ex), n + 1, out_row_ptr, st));
     h->launches += 9;
     unsigned* p_status = reinterpret_cast<unsigned*>(p_ll + 1);
-    TSG_CHECK(cudaMemcpyAsync(p_ll, b + L.ex + 8 * n, 8, cudaMemcpyDeviceToHost, st));
-    TSG_CHECK(cudaMemcpyAsync(p_status, h->status.p, 4, cudaMemcpyDeviceToHost, st));
+    TSG_CHECK(readback(h, p_ll, b + L.ex + 8 * n, 8, st));
+    TSG_CHECK(readback(h, p_status, h->status.p, 4, st));
     TSG_CHECK(cudaStreamSynchronize(st));
     if (*p_status) {
         TSG_CHECK(cudaMemsetAsync(h->status.p, 0, 4, st));
@@ -1497,9 +1581,10 @@ spgemm_status spgemm_launch_count(const spgemm_handle* h, int64_t* count) {
 spgemm_status spgemm_device_status(spgemm_handle* h) {
     if (!h) return SPGEMM_ERR_INVALID_ARG;
     if (!h->status.p) return SPGEMM_OK;
+    TSG_TRY(grow_pinned(h, 16));
+    TSG_CHECK(readback(h, h->pinned, h->status.p, 4, h->last_stream));
     TSG_CHECK(cudaStreamSynchronize(h->last_stream));
-    unsigned st = 0;
-    TSG_CHECK(cudaMemcpy(&st, h->status.p, 4, cudaMemcpyDeviceToHost));
+    const unsigned st = *static_cast<const unsigned*>(h->pinned);
     TSG_CHECK(cudaMemset(h->status.p, 0, 4));
     if (st & kStatusNotCanonical) return SPGEMM_ERR_NOT_CANONICAL;
     if (st & kStatusHashOverflow) return SPGEMM_ERR_HASH_OVERFLOW;

@@ -40,6 +40,10 @@ cudaError_t launch_rowptr(const GroupDev* groups, const long long* unit_base, in
 cudaError_t launch_validate(const int* rp, const int* col, int nrows, int ncols, int nnz, unsigned* status,
                             cudaStream_t s);
 
+// device-to-host read of `bytes` (a multiple of 4, at most 1 MiB) into mapped
+// page-locked memory by a kernel on stream s (rows_misc.cu)
+cudaError_t launch_readback(void* dst_mapped, const void* src, size_t bytes, cudaStream_t s);
+
 // row kernels
 struct RowLaunchArgs {
     const InstDev* inst;

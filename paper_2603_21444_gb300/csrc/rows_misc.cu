@@ -265,4 +265,19 @@ cudaError_t launch_validate(const int* rp, const int* col, int nrows, int ncols,
     return cudaGetLastError();
 }
 
+// Small device-to-host reads (counts, histograms, status words) stored by a
+// kernel into mapped page-locked memory: a copy-engine read would queue
+// behind whatever large device-to-host copy another stream has in flight.
+__global__ void k_readback(const unsigned* __restrict__ src, unsigned* dst, int nwords) {
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_readback(void* dst_mapped, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    if (bytes % 4 || bytes > (size_t(1) << 20)) return cudaErrorInvalidValue;
+    k_readback<<<1, 256, 0, s>>>(static_cast<const unsigned*>(src), static_cast<unsigned*>(dst_mapped),
+                                 (int)(bytes / 4));
+    return cudaGetLastError();
+}
+
 }  // namespace tsg

@@ -65,3 +65,71 @@ def test_host_product_empty_and_tiny(tsg):
     C = tsg.spgemm_host(host(tsg, A1), host(tsg, B1), h, panels=16)
     assert C.row_ptr.tolist() == [0, 2] and C.col.tolist() == [0, 1] and C.val.tolist() == [11.0, 10.0]
     h.close()
+
+
+def test_host_product_with_input_checks(tsg):
+    # the panels' row_ptr views start at absolute offsets: with input checks
+    # on, the whole matrices are checked once and the panels run unchecked
+    import ctypes
+    from paper_2603_21444_gb300 import _abi
+    A = gen.er_variable(4000, 3000, 20, 31, np.float64, "normal", p_empty=0.05)
+    B = gen.er_variable(3000, 3500, 20, 32, np.float64, "normal", p_empty=0.05)
+    ref, _ = oracle.spgemm(A, B)
+    h = tsg.Handle()
+    t = tsg.default_tune()
+    t.validate = 1
+    h.set_tune(t)
+    C = tsg.spgemm_host(host(tsg, A), host(tsg, B), h, panels=8)
+    assert np.array_equal(C.col.numpy(), ref.col) and np.array_equal(C.val.numpy(), ref.val)
+    # numeric on other host copies of the same matrices than the sizing call
+    # saw: indices copied and checked again
+    hA2, hB2 = host(tsg, A), host(tsg, B)
+    C.col.zero_()
+    C.val.zero_()
+    ain, bin_, cout = hA2.as_in(), hB2.as_in(), C.as_out()
+    _abi.check(_abi.lib().spgemm_host_numeric(h.ptr, _abi.F64, ctypes.byref(ain), ctypes.byref(bin_),
+                                              ctypes.byref(cout), 5, ctypes.c_void_p(0)), "spgemm_host_numeric")
+    assert np.array_equal(C.col.numpy(), ref.col) and np.array_equal(C.val.numpy(), ref.val)
+    # a column index out of range is reported, not read
+    Bad = gen.CSR(B.nrows, B.ncols, B.rowptr.copy(), B.col.copy(), B.val.copy())
+    Bad.col[len(Bad.col) // 2] = B.ncols + 7
+    with pytest.raises(RuntimeError):
+        tsg.spgemm_host(host(tsg, A), host(tsg, Bad), h, panels=4)
+    assert h.device_status() == 0
+    h.set_tune(None)
+    h.close()
+
+
+def test_host_numeric_repeated_with_new_values(tsg):
+    # the sizing call uploads the values for the numeric call right after it;
+    # a later numeric call on the same arrays copies the (changed) values again
+    import ctypes
+    from paper_2603_21444_gb300 import _abi
+    A = gen.er_variable(2500, 2000, 24, 51, np.float64, "normal", p_empty=0.05)
+    B = gen.er_variable(2000, 2200, 24, 52, np.float64, "normal", p_empty=0.05)
+    hA, hB = host(tsg, A), host(tsg, B)
+    h = tsg.Handle()
+    C = tsg.spgemm_host(hA, hB, h, panels=6)
+    ref, _ = oracle.spgemm(A, B)
+    assert np.array_equal(C.val.numpy(), ref.val)
+    B2 = gen.CSR(B.nrows, B.ncols, B.rowptr, B.col, -3.0 * B.val + 0.5)
+    hB.val.copy_(torch.from_numpy(B2.val))
+    ain, bin_, cout = hA.as_in(), hB.as_in(), C.as_out()
+    for panels in (1, 7):
+        C.val.zero_()
+        _abi.check(_abi.lib().spgemm_host_numeric(h.ptr, _abi.F64, ctypes.byref(ain), ctypes.byref(bin_),
+                                                  ctypes.byref(cout), panels, ctypes.c_void_p(0)), "spgemm_host_numeric")
+        ref2, _ = oracle.spgemm(A, B2)
+        assert np.array_equal(C.col.numpy(), ref2.col) and np.array_equal(C.val.numpy(), ref2.val)
+    # sizing without the values (-1), then the numeric call copies them
+    nnz = ctypes.c_int64()
+    _abi.check(_abi.lib().spgemm_host_symbolic(h.ptr, -1, ctypes.byref(ain), ctypes.byref(bin_),
+                                               ctypes.c_void_p(C.row_ptr.data_ptr()), ctypes.byref(nnz),
+                                               ctypes.c_void_p(0)), "spgemm_host_symbolic")
+    assert nnz.value == C.nnz
+    C.val.zero_()
+    _abi.check(_abi.lib().spgemm_host_numeric(h.ptr, _abi.F64, ctypes.byref(ain), ctypes.byref(bin_),
+                                              ctypes.byref(cout), 3, ctypes.c_void_p(0)), "spgemm_host_numeric")
+    assert np.array_equal(C.val.numpy(), ref2.val)
+    assert h.device_status() == 0
+    h.close()
