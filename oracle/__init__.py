@@ -407,6 +407,7 @@ def mcl_select(cols: np.ndarray, e: np.ndarray, inflation: float = 2.0, prune: f
         order = np.lexsort((cols, -v))
         keep = np.zeros_like(keep)
         keep[order[0]] = True
+        cuts["largest"] = float(v[order[0]])
     elif keep.sum() > topk:
         idx = np.nonzero(keep)[0]
         order = idx[np.lexsort((cols[idx], -v[idx]))]

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -1501,16 +1502,26 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     const long long stride = (n + 31) & ~31ll;
     const long long bm_words = stride / 32;
     const int slots = (int)std::min<long long>(n, (long long)h->sms * 4);
-    const size_t per = 8 * stride + 4 * stride + 4 * bm_words;
-    if (h->mcl_acc.n < per * slots) {
-        TSG_TRY(grow(h, h->mcl_acc, per * slots));
+    // candidate list per block: the entries with v >= prune number at most
+    // about 1 / prune (the v of a row sum to 1); twice that, and at least
+    // 4096, bounds it with room (a row beyond it is reported, not written)
+    long long ccap = stride;
+    if (prm->prune > 0.0 && 2.0 / prm->prune < (double)stride)
+        ccap = std::max<long long>(4096, (long long)std::ceil(2.0 / prm->prune));
+    ccap = std::min(ccap, stride);
+    const size_t o_bm = 12 * (size_t)stride * slots;
+    const size_t o_ck = align16(o_bm + 4 * (size_t)bm_words * slots);
+    const size_t o_cc = o_ck + 8 * (size_t)ccap * slots;
+    const size_t acc_bytes = o_cc + 4 * (size_t)ccap * slots;
+    if (h->mcl_acc.n < acc_bytes) {
+        TSG_TRY(grow(h, h->mcl_acc, acc_bytes));
         h->mcl_acc_key = -1;
     }
     // the kernel leaves the dense values and the bitmap zero after every row;
     // a different n moves the regions, so they are cleared then
     const long long key = stride * 4096 + slots;
     if (h->mcl_acc_key != key) {
-        TSG_CHECK(cudaMemsetAsync(h->mcl_acc.p, 0, per * slots, st));
+        TSG_CHECK(cudaMemsetAsync(h->mcl_acc.p, 0, o_ck, st));
         h->mcl_acc_key = key;
     }
     char* acc = static_cast<char*>(h->mcl_acc.p);
@@ -1527,7 +1538,10 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     ml.kept = reinterpret_cast<int*>(b + L.kept);
     ml.dense = reinterpret_cast<double*>(acc);
     ml.touched = reinterpret_cast<int*>(acc + 8 * stride * slots);
-    ml.bitmap = reinterpret_cast<unsigned*>(acc + 12 * stride * slots);
+    ml.bitmap = reinterpret_cast<unsigned*>(acc + o_bm);
+    ml.ckey = reinterpret_cast<unsigned long long*>(acc + o_ck);
+    ml.ccol = reinterpret_cast<int*>(acc + o_cc);
+    ml.ccap = (int)ccap;
     ml.stride = stride;
     ml.bm_words = bm_words;
     ml.row_counter = reinterpret_cast<int*>(b + L.ctr);

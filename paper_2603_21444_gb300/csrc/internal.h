@@ -122,6 +122,9 @@ struct MclLaunch {
     double* dense;
     unsigned* bitmap;
     int* touched;
+    unsigned long long* ckey;
+    int* ccol;
+    int ccap;
     long long stride;
     long long bm_words;
     int* row_counter;

@@ -14,7 +14,12 @@
 //   write     the kept entries sorted by column (bitonic sort in shared
 //             memory) at the row's upper-bound slot min(u_r, k)
 // A second kernel compacts the kept rows into the caller's CSR.
-// All keep/drop decisions are taken in double.
+// All keep/drop decisions are taken in double.  The double pipe is narrow on
+// this part, so each touched entry costs one square, one add and two
+// compares per pass: the quotient v = w / s is formed only for the
+// entries that can reach the prune or the maximum, and the prune survivors
+// (at most about 1 / prune of them, as the v sum to 1) go to a compact
+// candidate list that the top-k passes and the gather read.
 #include <algorithm>
 
 #include "internal.h"
@@ -23,6 +28,12 @@ namespace tsg {
 
 constexpr int kMclThreads = 256;
 constexpr int kMclMaxK = 1024;
+constexpr int kMclUnroll = 4;
+
+// fire-and-forget double add in L2 (no value returned to the thread)
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
 
 __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 #pragma unroll
@@ -40,6 +51,19 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     }
     __syncthreads();
     t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = sh[0];
+    for (int i = 1; i < kMclThreads / 32; ++i) t = fmax(t, sh[i]);
     __syncthreads();
     return t;
 }
@@ -76,6 +100,9 @@ struct MclArgs {
     double* dense;            // per block: n doubles
     unsigned* bitmap;         // per block: ceil(n / 32) words
     int* touched;             // per block: n ints
+    unsigned long long* ckey; // per block: ccap candidate values (double bits) ...
+    int* ccol;                // ... and their columns
+    int ccap;
     long long stride;         // n rounded up
     long long bm_words;
     int* row_counter;
@@ -90,6 +117,7 @@ struct MclShared {
     unsigned long long prefix;
     int kk;
     int bestj;
+    double bestv;
     double red[32];
     int ired[32];
     unsigned hist[256];
@@ -119,44 +147,83 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
             const int k = __ldg(a.col + e);
             const float av = __ldg(a.val + e);
             const int f0 = __ldg(a.rp + k), f1 = __ldg(a.rp + k + 1);
-            for (int f = f0 + lane; f < f1; f += 32) {
-                const int j = __ldg(a.col + f);
-                const double p = (double)__fmul_rn(av, __ldg(a.val + f));
-                atomicAdd(D + j, p);
-                const unsigned bit = 1u << (j & 31);
-                if (!(atomicOr(BM + (j >> 5), bit) & bit)) L[atomicAdd(&sh.cnt, 1)] = j;
+            // four products per lane in flight: the bitmap's fetch-or must
+            // return before its column can be listed, so its round trips
+            // are overlapped four at a time; the sums need no return
+            for (int f = f0 + lane; f < f1; f += 32 * kMclUnroll) {
+                int jj[kMclUnroll];
+                unsigned old[kMclUnroll];
+#pragma unroll
+                for (int u = 0; u < kMclUnroll; ++u) {
+                    const int g = f + 32 * u;
+                    jj[u] = g < f1 ? __ldg(a.col + g) : -1;
+                    if (jj[u] >= 0) {
+                        const double p = (double)__fmul_rn(av, __ldg(a.val + g));
+                        red_add_f64(D + jj[u], p);
+                        old[u] = atomicOr(BM + (jj[u] >> 5), 1u << (jj[u] & 31));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kMclUnroll; ++u)
+                    if (jj[u] >= 0 && !(old[u] & (1u << (jj[u] & 31)))) L[atomicAdd(&sh.cnt, 1)] = jj[u];
             }
         }
         __threadfence();
         __syncthreads();
         const int c = sh.cnt;
 
-        // ---- inflation: v_j = w_j / sum w
-        double loc = 0.0;
+        // ---- inflation: w_j = e_j^r; s = sum w (w is formed again from e
+        // in the next pass rather than stored and reloaded)
+        double loc = 0.0, wtop = 0.0;
         for (int i = tid; i < c; i += kMclThreads) {
             const double x = __ldcg(D + L[i]);
-            loc += square ? x * x : pow(x, a.inflation);
+            const double w = square ? x * x : pow(x, a.inflation);
+            loc += w;
+            wtop = fmax(wtop, w);
         }
         const double s = block_sum_d(loc, sh.red);
-        auto vof = [&](int j) {
-            const double x = __ldcg(D + j);
-            return (square ? x * x : pow(x, a.inflation)) / s;
-        };
+        const double wmax = block_max_d(wtop, sh.red);
 
-        // ---- prune count and the largest entry (ties: smaller column)
-        int nk = 0;
+        // ---- v_j = w_j / s; candidates v_j >= prune; the largest v (ties:
+        // smaller column).  With s > 0 the division is monotone, so only the
+        // entries whose w is within 2^-45 (relative) of prune * s or of the
+        // largest w can reach the prune or the maximum: the others are
+        // skipped without dividing (their rounded quotient stays below).
+        // (normal-range products only: there the two roundings stay far
+        // inside the 2^-45 margin)
+        const bool filt = a.prune >= 0.0 && s > 0.0 && s <= 1.7e308 && wmax >= 0x1p-1000 && wmax <= 1.7e308 &&
+                          (a.prune == 0.0 || a.prune * s >= 0x1p-1000);
+        const double wlo = filt ? a.prune * s * (1.0 - 0x1p-45) : 0.0;
+        const double whi = filt ? wmax * (1.0 - 0x1p-45) : 0.0;
+        unsigned long long* CK = a.ckey + (long long)blockIdx.x * a.ccap;
+        int* CC = a.ccol + (long long)blockIdx.x * a.ccap;
+        if (tid == 0) sh.cnt = 0;
+        __syncthreads();
         double vmax = -1.0;
         int jmax = 0x7fffffff;
         for (int i = tid; i < c; i += kMclThreads) {
             const int j = L[i];
-            const double v = vof(j);
-            nk += v >= a.prune;
+            const double x = __ldcg(D + j);
+            const double w = square ? x * x : pow(x, a.inflation);
+            if (filt && !(w >= wlo) && !(w >= whi)) continue;
+            const double v = w / s;
+            if (v >= a.prune) {
+                const int q = atomicAdd(&sh.cnt, 1);
+                if (q < a.ccap) {
+                    CK[q] = (unsigned long long)__double_as_longlong(v);
+                    CC[q] = j;
+                }
+            }
             if (v > vmax || (v == vmax && j < jmax)) {
                 vmax = v;
                 jmax = j;
             }
         }
-        const int nkeep = block_sum_i(nk, sh.ired);
+        __syncthreads();
+        const int nkeep = sh.cnt;
+        const int ncand = nkeep < a.ccap ? nkeep : a.ccap;
+        if (tid == 0 && nkeep > a.ccap) atomicOr(a.status, kStatusInternal);
+
         // arg-max over the block: the largest double, then the smallest column
         {
             double bv = vmax;
@@ -184,16 +251,18 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
                         gj = sh.ired[w];
                     }
                 sh.bestj = gj;
+                sh.bestv = gv;
             }
             __syncthreads();
         }
 
         // ---- the keep rule: mode 0 prune only, 1 largest only, 2 top-k
-        int mode = nkeep == 0 ? 1 : (nkeep > a.topk ? 2 : 0);
+        const int mode = nkeep == 0 ? 1 : (nkeep > a.topk ? 2 : 0);
         unsigned long long tkey = 0;  // top-k: the k-th largest value's bits
         int tie_j = 0x7fffffff;       // and the last column kept among ties
         if (mode == 2) {
-            // radix selection of the k-th largest key among kept candidates
+            // radix selection of the k-th largest key among the candidates
+            // (non-negative doubles: the bit patterns order as the values)
             if (tid == 0) {
                 sh.prefix = 0ull;
                 sh.kk = a.topk;
@@ -203,10 +272,8 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
                 for (int b = tid; b < 256; b += kMclThreads) sh.hist[b] = 0u;
                 __syncthreads();
                 const unsigned long long pre = sh.prefix;
-                for (int i = tid; i < c; i += kMclThreads) {
-                    const double v = vof(L[i]);
-                    if (v < a.prune) continue;
-                    const unsigned long long key = (unsigned long long)__double_as_longlong(v);
+                for (int q = tid; q < ncand; q += kMclThreads) {
+                    const unsigned long long key = CK[q];
                     if ((key & mask) == pre) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
                 }
                 __syncthreads();
@@ -237,11 +304,10 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
                 for (int b = tid; b < 256; b += kMclThreads) sh.hist[b] = 0u;
                 __syncthreads();
                 const unsigned pre = (unsigned)sh.prefix;
-                for (int i = tid; i < c; i += kMclThreads) {
-                    const int j = L[i];
-                    const double v = vof(j);
-                    if ((unsigned long long)__double_as_longlong(v) != tkey) continue;
-                    if (((unsigned)j & jmask) == pre) atomicAdd(&sh.hist[((unsigned)j >> shift) & 255u], 1u);
+                for (int q = tid; q < ncand; q += kMclThreads) {
+                    if (CK[q] != tkey) continue;
+                    const unsigned j = (unsigned)CC[q];
+                    if ((j & jmask) == pre) atomicAdd(&sh.hist[(j >> shift) & 255u], 1u);
                 }
                 __syncthreads();
                 if (tid == 0) {
@@ -260,32 +326,36 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
             tie_j = (int)sh.prefix;
         }
         const int bestj = sh.bestj;
-        auto keep = [&](int j, double v) {
-            if (mode == 1) return j == bestj;
-            if (v < a.prune) return false;
+        auto kept_q = [&](int q) {
             if (mode == 0) return true;
-            const unsigned long long key = (unsigned long long)__double_as_longlong(v);
-            return key > tkey || (key == tkey && j <= tie_j);
+            const unsigned long long key = CK[q];
+            return key > tkey || (key == tkey && CC[q] <= tie_j);
         };
 
         // ---- renormalise over the kept entries and gather them
         double kl = 0.0;
-        for (int i = tid; i < c; i += kMclThreads) {
-            const int j = L[i];
-            const double v = vof(j);
-            if (keep(j, v)) kl += v;
+        if (mode == 1) {
+            if (tid == 0 && bestj != 0x7fffffff) kl = sh.bestv;
+        } else {
+            for (int q = tid; q < ncand; q += kMclThreads)
+                if (kept_q(q)) kl += __longlong_as_double((long long)CK[q]);
         }
         const double t = block_sum_d(kl, sh.red);
         if (tid == 0) sh.cnt = 0;
         __syncthreads();
-        for (int i = tid; i < c; i += kMclThreads) {
-            const int j = L[i];
-            const double v = vof(j);
-            if (keep(j, v)) {
-                const int q = atomicAdd(&sh.cnt, 1);
-                if (q < kMclMaxK) {
-                    sh.kcol[q] = j;
-                    sh.kval[q] = (float)(v / t);
+        if (mode == 1) {
+            if (tid == 0 && bestj != 0x7fffffff) {
+                sh.kcol[0] = bestj;
+                sh.kval[0] = (float)(sh.bestv / t);
+                sh.cnt = 1;
+            }
+        } else {
+            for (int q = tid; q < ncand; q += kMclThreads) {
+                if (!kept_q(q)) continue;
+                const int o = atomicAdd(&sh.cnt, 1);
+                if (o < kMclMaxK) {
+                    sh.kcol[o] = CC[q];
+                    sh.kval[o] = (float)(__longlong_as_double((long long)CK[q]) / t);
                 }
             }
         }
@@ -326,7 +396,9 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
             }
             if (tid == 0) a.kept[r] = nout;
         }
-        // ---- clear the accumulator for the next row
+        // ---- clear the accumulator and the bitmap for the next row (a pass
+        // of its own: a store right behind the load of the same word in the
+        // candidate pass held every iteration for the load's round trip)
         __syncthreads();
         for (int i = tid; i < c; i += kMclThreads) {
             const int j = L[i];
@@ -382,6 +454,9 @@ cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s) {
     a.dense = l.dense;
     a.bitmap = l.bitmap;
     a.touched = l.touched;
+    a.ckey = l.ckey;
+    a.ccol = l.ccol;
+    a.ccap = l.ccap;
     a.stride = l.stride;
     a.bm_words = l.bm_words;
     a.row_counter = l.row_counter;

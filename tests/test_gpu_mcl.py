@@ -1,8 +1,9 @@
 """GPU parity of the fused Markov-clustering iteration (Sec. 5.6) against the
 oracle.  Parity is per iteration: the oracle takes the GPU's input iterate.
 Decisions are taken in double on both sides; an entry whose v lies within
-1e-9 (relative) of a cut (the prune threshold or the k-th largest value) may
-legitimately fall on either side and is excluded from the pattern check."""
+1e-9 (relative) of a cut (the prune threshold, the k-th largest value, or
+the largest value when only that one is kept) may legitimately fall on
+either side and is excluded from the pattern check."""
 import numpy as np
 import pytest
 import torch
@@ -43,7 +44,7 @@ def compare_rows(got, ref_rows, rel_cut=1e-9):
         either = set()
         if "v" in cuts:
             v, cc = cuts["v"], cuts["cols"]
-            for key in ("prune", "topk_value"):
+            for key in ("prune", "topk_value", "largest"):
                 if key in cuts:
                     near = np.abs(v - cuts[key]) <= rel_cut * cuts[key]
                     either |= set(cc[near].tolist())
@@ -136,3 +137,18 @@ def test_handle_reused_across_graph_sizes(tsg, handle):
         torch.cuda.synchronize()
         ref = oracle.mcl_step(Mt, topk=200, rows=np.arange(Mt.nrows))
         compare_rows(R.to_host(), ref)
+
+
+@pytest.mark.parametrize("inflation,prune,topk", [(1.5, 0.0, 1000), (2.0, 0.9, 1000), (3.0, 1e-3, 5), (2.0, 0.0, 30)])
+def test_keep_rules_and_inflations(tsg, handle, inflation, prune, topk):
+    # prune 0: every touched entry is a candidate (the candidate list as
+    # long as the row); prune 0.9: most rows keep only their largest entry;
+    # inflation 1.5 / 3 take the power path of the quotient filter
+    Mt = gen.rmat_stochastic(scale=11, edge_factor=16, seed=9)
+    R = tsg.mcl_step(tsg.DeviceCSR.from_host(Mt), inflation=inflation, prune=prune, topk=topk, handle=handle)
+    torch.cuda.synchronize()
+    ref = oracle.mcl_step(Mt, inflation=inflation, prune=prune, topk=topk, rows=np.arange(Mt.nrows))
+    compare_rows(R.to_host(), ref)
+    rp, _, val = R.to_host()
+    assert np.all(np.diff(rp) >= 1) and np.all(np.diff(rp) <= topk)
+    assert np.allclose(np.add.reduceat(val.astype(np.float64), rp[:-1]), 1.0, atol=1e-5)
