@@ -470,7 +470,9 @@ typedef struct {
     double inflation;  /* r of the inflation step (2) */
     double prune;      /* drop v_j below this (1e-4) */
     int32_t topk;      /* keep at most this many per row (1000) */
-    int32_t reserved;  /* 0 */
+    int32_t heavy;     /* rows with at least this many products run in batches
+                          of a few rows on dense accumulators resident in L2
+                          (0: max(4096, n); < 0: never; with prune 0 never) */
 } spgemm_mcl_params;
 
 spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const spgemm_mcl_params* prm,

@@ -43,7 +43,7 @@ class CsrOut(ctypes.Structure):
 
 class MclParams(ctypes.Structure):
     _fields_ = [("inflation", ctypes.c_double), ("prune", ctypes.c_double), ("topk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("heavy", ctypes.c_int32)]
 
 
 class Tune(ctypes.Structure):

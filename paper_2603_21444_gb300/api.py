@@ -664,12 +664,14 @@ class TridentPlan:
 # ------------------------------------------------------- Markov clustering
 
 def mcl_step(Mt: DeviceCSR, inflation: float = 2.0, prune: float = 1e-4, topk: int = 1000,
-             handle: Handle | None = None, stream=None) -> DeviceCSR:
+             handle: Handle | None = None, stream=None, heavy: int = 0) -> DeviceCSR:
     """One Markov-clustering iteration (Sec. 5.6) on the transposed
     column-stochastic matrix: expansion fused with inflation, pruning, top-k
-    and renormalisation (``spgemm_mcl_expand`` / ``spgemm_mcl_collect``)."""
+    and renormalisation (``spgemm_mcl_expand`` / ``spgemm_mcl_collect``).
+    ``heavy``: rows with at least this many products take the batched
+    dense-accumulator path (0: the library's default, < 0: never)."""
     h = handle or default_handle()
-    prm = _abi.MclParams(float(inflation), float(prune), int(topk), 0)
+    prm = _abi.MclParams(float(inflation), float(prune), int(topk), int(heavy))
     dev = Mt.row_ptr.device
     rp = torch.empty(Mt.nrows + 1, dtype=torch.int32, device=dev)
     nnz = ctypes.c_int64()

@@ -64,6 +64,10 @@ struct spgemm_handle {
     DevBuf tr;      // transpose work and the A^T of the deterministic backward
     DevBuf mcl;     // Markov clustering: bounds, offsets, kept entries
     DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
+    DevBuf mcl_heavy;  // ... heavy-row flags and list, two buffers of batch accumulators
+    long long mcl_heavy_key = -1;  // layout whose batch accumulators are known to be zero
+    cudaStream_t mcl_side = nullptr;  // heavy-row selection, overlapping the next batch
+    cudaEvent_t mcl_ev[5] = {};       // batch ready (2), buffer cleared (2), join
     DevBuf perm;    // permutation: target hits, row lengths, scan, long-row list, ranks
     DevBuf hx;      // product from host memory: device copies of A, B and C's row_ptr
     DevBuf hc;      // ... and of C's columns and values
@@ -812,6 +816,13 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     if (h->tr.p) cudaFree(h->tr.p);
     if (h->mcl.p) cudaFree(h->mcl.p);
     if (h->mcl_acc.p) cudaFree(h->mcl_acc.p);
+    if (h->mcl_side) {
+        cudaStreamSynchronize(h->mcl_side);
+        cudaStreamDestroy(h->mcl_side);
+    }
+    for (cudaEvent_t e : h->mcl_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->mcl_heavy.p) cudaFree(h->mcl_heavy.p);
     if (h->perm.p) cudaFree(h->perm.p);
     if (h->hx.p) cudaFree(h->hx.p);
     if (h->hc.p) cudaFree(h->hc.p);
@@ -1549,7 +1560,84 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     ml.prune = prm->prune;
     ml.topk = prm->topk;
     ml.status = static_cast<unsigned*>(h->status.p);
+    // 2b. heavy rows (at least `thr` products; prm->heavy > 0 sets it,
+    // < 0 turns the path off): batches of R rows whose dense accumulators
+    // fit L2 together.  With prune 0 every touched column may be kept, which
+    // a dense scan cannot tell from an untouched one: the path is off then.
+    const long long thr = prm->heavy > 0 ? (long long)prm->heavy : std::max<long long>(4096, n);
+    const long long acc_row = 8 * stride;
+    const bool heavy_on = prm->heavy >= 0 && prm->prune > 0.0 && acc_row <= (64ll << 20);
+    int H = 0;
+    const int R = (int)std::max<long long>(1, std::min<long long>(kMclBatch, (48ll << 20) / acc_row));
+    const size_t o_hl = align16((size_t)n), o_hc = o_hl + align16(4 * (size_t)n);
+    const size_t o_sc = (size_t)R * acc_row;  // within a buffer: D | scalars | ck | cc | mlist
+    const size_t o_bck = o_sc + align16((size_t)R * (8 + 8 + 4 + 4 + 4));
+    const size_t o_bcc = o_bck + 8 * (size_t)R * ccap;
+    const size_t buf_bytes = align16(o_bcc + 4 * (size_t)R * ccap + 4 * (size_t)R * kMclMaxList);
+    const size_t o_buf = o_hc + 16;
+    // the flags, list, count and positivity word always; the two batch
+    // buffers when the path is on
+    const size_t heavy_bytes = heavy_on ? o_buf + 2 * buf_bytes : o_buf;
+    if (h->mcl_heavy.n < heavy_bytes) {
+        TSG_TRY(grow(h, h->mcl_heavy, heavy_bytes));
+        h->mcl_heavy_key = -1;
+    }
+    char* hv = static_cast<char*>(h->mcl_heavy.p);
+    TSG_CHECK(cudaMemsetAsync(hv + o_hc, 0, 16, st));
+    // every value in [2^-63, FLT_MAX]: products and sums stay positive, so
+    // a column's first add finds 0 (the expansion needs no bitmap)
+    TSG_CHECK(launch_mcl_check_positive(static_cast<const float*>(Mt->val), Mt->nnz, reinterpret_cast<int*>(hv + o_hc + 4),
+                                        h->sms, st));
+    ++h->launches;
+    if (heavy_on) {
+        const long long hkey = (long long)stride * 4096 * 32 + (long long)R * 4096 + (ccap & 4095);
+        if (h->mcl_heavy_key != hkey) {
+            for (int q = 0; q < 2; ++q) TSG_CHECK(cudaMemsetAsync(hv + o_buf + q * buf_bytes, 0, o_bck, st));
+            h->mcl_heavy_key = hkey;
+        }
+        TSG_CHECK(launch_mcl_heavy_mark(Mt->row_ptr, Mt->col_idx, (int)n, thr, reinterpret_cast<unsigned char*>(hv),
+                                        reinterpret_cast<int*>(hv + o_hl), reinterpret_cast<int*>(hv + o_hc), st));
+        ++h->launches;
+    }
+    TSG_CHECK(readback(h, p_ll + 2, hv + o_hc, 8, st));
+    TSG_CHECK(cudaStreamSynchronize(st));
+    H = heavy_on ? reinterpret_cast<const int*>(p_ll + 2)[0] : 0;
+    ml.positive = reinterpret_cast<const int*>(p_ll + 2)[1] == 0 ? 1 : 0;
+    ml.heavy = H > 0 ? reinterpret_cast<const unsigned char*>(hv) : nullptr;
     TSG_CHECK(launch_mcl_rows(ml, slots, st));
+    if (H > 0) {
+        if (!h->mcl_side) TSG_CHECK(cudaStreamCreateWithFlags(&h->mcl_side, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : h->mcl_ev)
+            if (!e) TSG_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        const int* hlist = reinterpret_cast<const int*>(hv + o_hl);
+        for (int i = 0, bi = 0; i < H; i += R, ++bi) {
+            const int q = bi & 1;
+            char* bb = hv + o_buf + q * buf_bytes;
+            MclHeavyLaunch hb;
+            hb.rows = hlist + i;
+            hb.nb = std::min(R, H - i);
+            hb.D = reinterpret_cast<double*>(bb);
+            hb.s = reinterpret_cast<double*>(bb + o_sc);
+            hb.wmax = reinterpret_cast<unsigned long long*>(bb + o_sc + 8 * R);
+            hb.flags = reinterpret_cast<unsigned*>(bb + o_sc + 16 * R);
+            hb.ncand = reinterpret_cast<int*>(bb + o_sc + 20 * R);
+            hb.nmax = reinterpret_cast<int*>(bb + o_sc + 24 * R);
+            hb.ck = reinterpret_cast<unsigned long long*>(bb + o_bck);
+            hb.cc = reinterpret_cast<int*>(bb + o_bcc);
+            hb.mlist = reinterpret_cast<int*>(bb + o_bcc + 4 * (size_t)R * ccap);
+            // the buffer's previous batch must be selected and cleared
+            if (bi >= 2) TSG_CHECK(cudaStreamWaitEvent(st, h->mcl_ev[2 + q], 0));
+            TSG_CHECK(launch_mcl_heavy_batch(ml, hb, h->sms, st));
+            TSG_CHECK(cudaEventRecord(h->mcl_ev[q], st));
+            TSG_CHECK(cudaStreamWaitEvent(h->mcl_side, h->mcl_ev[q], 0));
+            TSG_CHECK(launch_mcl_heavy_select(ml, hb, h->mcl_side));
+            TSG_CHECK(cudaMemsetAsync(bb, 0, o_bck, h->mcl_side));
+            TSG_CHECK(cudaEventRecord(h->mcl_ev[2 + q], h->mcl_side));
+            h->launches += 4;
+        }
+        TSG_CHECK(cudaEventRecord(h->mcl_ev[4], h->mcl_side));
+        TSG_CHECK(cudaStreamWaitEvent(st, h->mcl_ev[4], 0));
+    }
     // 3. row pointers of the next iterate
     TSG_CHECK(launch_scan(reinterpret_cast<int*>(b + L.kept), n, reinterpret_cast<long long*>(b + L.bsum),
                           reinterpret_cast<long long*>(b + L.ex), st));

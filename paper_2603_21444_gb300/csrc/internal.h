@@ -132,7 +132,31 @@ struct MclLaunch {
     double prune;
     int topk;
     unsigned* status;
+    const unsigned char* heavy = nullptr;  // rows left to the batched path
+    int positive = 0;                      // every value in [2^-63, FLT_MAX]
 };
+// batched heavy rows: at most kMclBatch rows per batch, each with a dense
+// accumulator; kMclMaxList near-max columns kept per row
+constexpr int kMclBatch = 16;
+constexpr int kMclMaxList = 1024;
+struct MclHeavyLaunch {
+    const int* rows;
+    int nb;
+    double* D;
+    double* s;
+    unsigned long long* wmax;
+    unsigned* flags;
+    int* ncand;
+    int* nmax;
+    unsigned long long* ck;
+    int* cc;
+    int* mlist;
+};
+cudaError_t launch_mcl_check_positive(const float* val, long long nnz, int* flag, int sms, cudaStream_t s);
+cudaError_t launch_mcl_heavy_mark(const int* rp, const int* col, int n, long long threshold, unsigned char* flags,
+                                  int* list, int* count, cudaStream_t s);
+cudaError_t launch_mcl_heavy_batch(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s);
+cudaError_t launch_mcl_heavy_select(const MclLaunch& l, const MclHeavyLaunch& hb, cudaStream_t s);
 cudaError_t launch_mcl_bounds(const int* rp, const int* col, int n, int topk, int* ub, cudaStream_t s);
 cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s);
 cudaError_t launch_mcl_collect(int n, const long long* ub_off, const int* tmp_col, const float* tmp_val,

@@ -152,3 +152,65 @@ def test_keep_rules_and_inflations(tsg, handle, inflation, prune, topk):
     rp, _, val = R.to_host()
     assert np.all(np.diff(rp) >= 1) and np.all(np.diff(rp) <= topk)
     assert np.allclose(np.add.reduceat(val.astype(np.float64), rp[:-1]), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("heavy", [1, 2048, -1])
+@pytest.mark.parametrize("topk", [1000, 25])
+def test_heavy_row_batches(tsg, handle, heavy, topk):
+    # heavy = 1: every row with a product runs in the batched dense path;
+    # 2048: the hubs only; -1: none (the per-block path alone)
+    Mt = gen.rmat_stochastic(scale=12, edge_factor=16, seed=13)
+    R = tsg.mcl_step(tsg.DeviceCSR.from_host(Mt), topk=topk, handle=handle, heavy=heavy)
+    torch.cuda.synchronize()
+    ref = oracle.mcl_step(Mt, topk=topk, rows=np.arange(Mt.nrows))
+    compare_rows(R.to_host(), ref)
+
+
+@pytest.mark.parametrize("inflation,prune,topk", [(2.0, 0.9, 1000), (3.0, 1e-3, 5), (1.5, 1e-4, 1)])
+def test_heavy_row_keep_rules(tsg, handle, inflation, prune, topk):
+    Mt = gen.rmat_stochastic(scale=11, edge_factor=16, seed=21)
+    R = tsg.mcl_step(tsg.DeviceCSR.from_host(Mt), inflation=inflation, prune=prune, topk=topk, handle=handle, heavy=1)
+    torch.cuda.synchronize()
+    ref = oracle.mcl_step(Mt, inflation=inflation, prune=prune, topk=topk, rows=np.arange(Mt.nrows))
+    compare_rows(R.to_host(), ref)
+
+
+def test_heavy_row_all_equal_values(tsg, handle):
+    # blocks of b columns holding 1/b each: every expanded entry of a row is
+    # 1/b.  b = 1500 with prune 0.01: nothing reaches the prune, all 1500
+    # entries tie for the largest (more than the near-max list holds), and
+    # the smallest column is kept; b = 1200 with prune 1e-4 and topk 1000:
+    # the top-k cut falls inside a tie, the 1000 smallest columns are kept
+    for b, prune, kept in ((1500, 0.01, 1), (1200, 1e-4, 1000)):
+        rows = [list(range(7, 7 + b))] * b
+        n = 7 + b
+        rp = np.zeros(n + 1, dtype=np.int64)
+        rp[8:] = np.cumsum([b] * b)
+        U = gen.CSR(n, n, rp, np.concatenate(rows).astype(np.int32), np.full(b * b, 1.0 / b, dtype=np.float32))
+        for heavy in (1, -1):
+            R = tsg.mcl_step(tsg.DeviceCSR.from_host(U), prune=prune, topk=1000, handle=handle, heavy=heavy)
+            rpo, col, val = R.to_host()
+            assert np.all(np.diff(rpo)[:7] == 0) and np.all(np.diff(rpo)[7:] == kept), (b, heavy)
+            for r in (7, 7 + b // 2, n - 1):
+                assert col[rpo[r]:rpo[r + 1]].tolist() == list(range(7, 7 + kept)), (b, heavy, r)
+                assert np.allclose(val[rpo[r]:rpo[r + 1]], 1.0 / kept, rtol=1e-6)
+
+
+@pytest.mark.parametrize("heavy", [-1, 1])
+def test_values_not_all_positive(tsg, handle, heavy):
+    # zero, negative and tiny values: a sum may be 0 while touched, so the
+    # expansion lists first touches with the bitmap instead of the add's
+    # old value (all-positive inputs take the bitmap-free path)
+    Mt = gen.rmat_stochastic(scale=11, edge_factor=16, seed=17)
+    val = Mt.val.copy()
+    val[::7] = 0.0
+    val[3::11] *= -1.0
+    val[5::13] = 1e-30
+    M2 = gen.CSR(Mt.nrows, Mt.ncols, Mt.rowptr, Mt.col, val.astype(np.float32))
+    R = tsg.mcl_step(tsg.DeviceCSR.from_host(M2), handle=handle, heavy=heavy)
+    torch.cuda.synchronize()
+    ref = oracle.mcl_step(M2, rows=np.arange(M2.nrows))
+    # a row whose products are all 0 has no defined v (0 / 0): left out
+    ref = {r: x for r, x in ref.items() if "v" not in x[2] or np.all(np.isfinite(x[2]["v"]))}
+    assert len(ref) > M2.nrows * 0.9
+    compare_rows(R.to_host(), ref)
