@@ -64,7 +64,8 @@ struct spgemm_handle {
     DevBuf tr;      // transpose work and the A^T of the deterministic backward
     DevBuf mcl;     // Markov clustering: bounds, offsets, kept entries
     DevBuf mcl_acc; // Markov clustering: per-block dense accumulators
-    DevBuf mcl_heavy;  // ... heavy-row flags and list, two buffers of batch accumulators
+    DevBuf mcl_heavy;  // ... row flags, heavy and bucket lists, two buffers of batch accumulators
+    DevBuf mcl_bucket; // ... bucketed rows: staging and emitted columns per block
     long long mcl_heavy_key = -1;  // layout whose batch accumulators are known to be zero
     cudaStream_t mcl_side = nullptr;  // heavy-row selection, overlapping the next batch
     cudaEvent_t mcl_ev[5] = {};       // batch ready (2), buffer cleared (2), join
@@ -823,6 +824,7 @@ spgemm_status spgemm_destroy(spgemm_handle* h) {
     for (cudaEvent_t e : h->mcl_ev)
         if (e) cudaEventDestroy(e);
     if (h->mcl_heavy.p) cudaFree(h->mcl_heavy.p);
+    if (h->mcl_bucket.p) cudaFree(h->mcl_bucket.p);
     if (h->perm.p) cudaFree(h->perm.p);
     if (h->hx.p) cudaFree(h->hx.p);
     if (h->hc.p) cudaFree(h->hc.p);
@@ -1569,42 +1571,70 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     const bool heavy_on = prm->heavy >= 0 && prm->prune > 0.0 && acc_row <= (64ll << 20);
     int H = 0;
     const int R = (int)std::max<long long>(1, std::min<long long>(kMclBatch, (48ll << 20) / acc_row));
-    const size_t o_hl = align16((size_t)n), o_hc = o_hl + align16(4 * (size_t)n);
+    // flags | heavy list | bucket list | hcount, notpos, bcount, bucket row counter | batch buffers
+    const size_t o_hl = align16((size_t)n), o_bl = o_hl + align16(4 * (size_t)n);
+    const size_t o_hc = o_bl + align16(4 * (size_t)n);
     const size_t o_sc = (size_t)R * acc_row;  // within a buffer: D | scalars | ck | cc | mlist
     const size_t o_bck = o_sc + align16((size_t)R * (8 + 8 + 4 + 4 + 4));
     const size_t o_bcc = o_bck + 8 * (size_t)R * ccap;
     const size_t buf_bytes = align16(o_bcc + 4 * (size_t)R * ccap + 4 * (size_t)R * kMclMaxList);
     const size_t o_buf = o_hc + 16;
-    // the flags, list, count and positivity word always; the two batch
-    // buffers when the path is on
     const size_t heavy_bytes = heavy_on ? o_buf + 2 * buf_bytes : o_buf;
     if (h->mcl_heavy.n < heavy_bytes) {
         TSG_TRY(grow(h, h->mcl_heavy, heavy_bytes));
         h->mcl_heavy_key = -1;
     }
     char* hv = static_cast<char*>(h->mcl_heavy.p);
-    TSG_CHECK(cudaMemsetAsync(hv + o_hc, 0, 16, st));
+    int* ctr4 = reinterpret_cast<int*>(hv + o_hc);
+    TSG_CHECK(cudaMemsetAsync(ctr4, 0, 16, st));
     // every value in [2^-63, FLT_MAX]: products and sums stay positive, so
-    // a column's first add finds 0 (the expansion needs no bitmap)
-    TSG_CHECK(launch_mcl_check_positive(static_cast<const float*>(Mt->val), Mt->nnz, reinterpret_cast<int*>(hv + o_hc + 4),
-                                        h->sms, st));
+    // a column's first add finds 0 (no bitmap), and the bucketed path applies
+    TSG_CHECK(launch_mcl_check_positive(static_cast<const float*>(Mt->val), Mt->nnz, ctr4 + 1, h->sms, st));
     ++h->launches;
+    // 2c. bucketed mid rows (4096 <= products < the staging capacity 2^20,
+    // below the heavy threshold): windows of 2^lw columns, at most 64 per
+    // row up to n = 2^18 and 4096 columns wide beyond
+    int lw = 5;
+    while (lw < 12 && (n >> lw) > 64) ++lw;
+    const int nbk = (int)((n + (1ll << lw) - 1) >> lw);
+    const int bps = nbk <= 2048 ? mcl_bucket_blocks_per_sm(lw, nbk) : 0;
+    const int bblocks = (int)std::min<long long>(slots, (long long)h->sms * std::min(bps, 4));
+    const long long bcap = heavy_on ? std::min<long long>(1ll << 20, thr) : (1ll << 20);
+    const long long blo = bblocks > 0 ? 4096 : (1ll << 62);
     if (heavy_on) {
         const long long hkey = (long long)stride * 4096 * 32 + (long long)R * 4096 + (ccap & 4095);
         if (h->mcl_heavy_key != hkey) {
             for (int q = 0; q < 2; ++q) TSG_CHECK(cudaMemsetAsync(hv + o_buf + q * buf_bytes, 0, o_bck, st));
             h->mcl_heavy_key = hkey;
         }
-        TSG_CHECK(launch_mcl_heavy_mark(Mt->row_ptr, Mt->col_idx, (int)n, thr, reinterpret_cast<unsigned char*>(hv),
-                                        reinterpret_cast<int*>(hv + o_hl), reinterpret_cast<int*>(hv + o_hc), st));
+    }
+    TSG_CHECK(launch_mcl_mark(Mt->row_ptr, Mt->col_idx, (int)n, heavy_on ? thr : (1ll << 62), blo, bcap, ctr4 + 1,
+                              reinterpret_cast<unsigned char*>(hv), reinterpret_cast<int*>(hv + o_hl), ctr4,
+                              reinterpret_cast<int*>(hv + o_bl), ctr4 + 2, st));
+    ++h->launches;
+    TSG_CHECK(readback(h, p_ll + 2, ctr4, 12, st));
+    TSG_CHECK(cudaStreamSynchronize(st));
+    const int* got = reinterpret_cast<const int*>(p_ll + 2);
+    H = got[0];
+    const int NBR = got[2];
+    ml.positive = got[1] == 0 ? 1 : 0;
+    ml.heavy = H + NBR > 0 ? reinterpret_cast<const unsigned char*>(hv) : nullptr;
+    TSG_CHECK(launch_mcl_rows(ml, slots, st));
+    if (NBR > 0) {
+        const size_t sbytes = (size_t)bblocks * bcap * 8, ebytes = (size_t)bblocks * bcap * 4;
+        TSG_TRY(grow(h, h->mcl_bucket, sbytes + ebytes));
+        MclBucketLaunch bl;
+        bl.list = reinterpret_cast<const int*>(hv + o_bl);
+        bl.count = NBR;
+        bl.counter = ctr4 + 3;
+        bl.stage = reinterpret_cast<int2*>(h->mcl_bucket.p);
+        bl.ej = reinterpret_cast<int*>(static_cast<char*>(h->mcl_bucket.p) + sbytes);
+        bl.cap = bcap;
+        bl.lw = lw;
+        bl.nbk = nbk;
+        TSG_CHECK(launch_mcl_bucket(ml, bl, bblocks, st));
         ++h->launches;
     }
-    TSG_CHECK(readback(h, p_ll + 2, hv + o_hc, 8, st));
-    TSG_CHECK(cudaStreamSynchronize(st));
-    H = heavy_on ? reinterpret_cast<const int*>(p_ll + 2)[0] : 0;
-    ml.positive = reinterpret_cast<const int*>(p_ll + 2)[1] == 0 ? 1 : 0;
-    ml.heavy = H > 0 ? reinterpret_cast<const unsigned char*>(hv) : nullptr;
-    TSG_CHECK(launch_mcl_rows(ml, slots, st));
     if (H > 0) {
         if (!h->mcl_side) TSG_CHECK(cudaStreamCreateWithFlags(&h->mcl_side, cudaStreamNonBlocking));
         for (cudaEvent_t& e : h->mcl_ev)

@@ -153,8 +153,23 @@ struct MclHeavyLaunch {
     int* mlist;
 };
 cudaError_t launch_mcl_check_positive(const float* val, long long nnz, int* flag, int sms, cudaStream_t s);
-cudaError_t launch_mcl_heavy_mark(const int* rp, const int* col, int n, long long threshold, unsigned char* flags,
-                                  int* list, int* count, cudaStream_t s);
+cudaError_t launch_mcl_mark(const int* rp, const int* col, int n, long long heavy, long long bucket_lo,
+                            long long bucket_hi, const int* notpos, unsigned char* flags, int* hlist, int* hcount,
+                            int* blist, int* bcount, cudaStream_t s);
+// bucketed mid rows: staging of cap entries per block, windows of 2^lw columns
+struct MclBucketLaunch {
+    const int* list;
+    int count;
+    int* counter;
+    int2* stage;
+    int* ej;
+    long long cap;
+    int lw;
+    int nbk;
+};
+size_t mcl_bucket_smem(int lw, int nbk);
+int mcl_bucket_blocks_per_sm(int lw, int nbk);
+cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int blocks, cudaStream_t s);
 cudaError_t launch_mcl_heavy_batch(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s);
 cudaError_t launch_mcl_heavy_select(const MclLaunch& l, const MclHeavyLaunch& hb, cudaStream_t s);
 cudaError_t launch_mcl_bounds(const int* rp, const int* col, int n, int topk, int* ub, cudaStream_t s);

@@ -493,6 +493,222 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
     }
 }
 
+// ------------------------------------------------------ bucketed mid rows
+//
+// Rows between the small and the heavy thresholds, positive values only.
+// The row's products are counted per column window of W = 2^lw columns,
+// scattered into a staging buffer in window order (column, float product:
+// 8 bytes), and each window is then summed in shared memory, where the add
+// that finds 0 lists the column; the window's entries are emitted as a
+// compact (column, e) list in column-window order, which the prune and
+// top-k passes read contiguously.  Every global access but the B-row reads
+// is a stream, where the per-block kernel's random adds into an 8 MB
+// accumulator miss L2.
+
+struct MclBucketArgs {
+    const int* list;     // the rows of this path
+    int count;           // how many
+    int* counter;        // next row to take
+    int2* stage;         // per block: cap entries (column, float product bits)
+    int* ej;             // per block: cap emitted columns (values overwrite stage)
+    long long cap;
+    int lw;              // log2 of the window width
+    int nbk;             // windows: ceil(n / W)
+};
+
+__global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclBucketArgs bk) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ MclShared sh;
+    __shared__ int s_row, s_lc[2];
+    const int W = 1 << bk.lw, NB = bk.nbk;
+    double* win = reinterpret_cast<double*>(dyn);
+    int* tl = reinterpret_cast<int*>(dyn + 8 * (size_t)W);
+    int* off = tl + W;     // NB + 1
+    int* cur = off + NB + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int2* stage = bk.stage + (long long)blockIdx.x * bk.cap;
+    double* ex = reinterpret_cast<double*>(stage);
+    int* ej = bk.ej + (long long)blockIdx.x * bk.cap;
+    unsigned long long* CK = a.ckey + (long long)blockIdx.x * a.ccap;
+    int* CC = a.ccol + (long long)blockIdx.x * a.ccap;
+    const bool square = a.inflation == 2.0;
+    for (int i = tid; i < W; i += kMclThreads) win[i] = 0.0;
+    if (tid == 0) {
+        s_lc[0] = 0;
+        s_lc[1] = 0;
+    }
+    for (;;) {
+        if (tid == 0) s_row = atomicAdd(bk.counter, 1);
+        for (int i = tid; i < NB; i += kMclThreads) cur[i] = 0;
+        __syncthreads();
+        const int q = s_row;
+        if (q >= bk.count) break;
+        const int r = bk.list[q];
+        const int e0 = __ldg(a.rp + r), e1 = __ldg(a.rp + r + 1);
+        // ---- products per window
+        for (int e = e0 + warp; e < e1; e += kMclThreads / 32) {
+            const int k = __ldg(a.col + e);
+            const int f0 = __ldg(a.rp + k), f1 = __ldg(a.rp + k + 1);
+            for (int f = f0 + lane; f < f1; f += 32) atomicAdd(cur + (__ldg(a.col + f) >> bk.lw), 1);
+        }
+        __syncthreads();
+        // ---- window offsets (one warp, 32 windows per step)
+        if (warp == 0) {
+            int run = 0;
+            for (int b0 = 0; b0 < NB; b0 += 32) {
+                const int b = b0 + lane;
+                const int v = b < NB ? cur[b] : 0;
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (b < NB) off[b] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) off[NB] = run;
+        }
+        __syncthreads();
+        for (int i = tid; i < NB; i += kMclThreads) cur[i] = off[i];
+        __syncthreads();
+        // ---- scatter the products in window order
+        for (int e = e0 + warp; e < e1; e += kMclThreads / 32) {
+            const int k = __ldg(a.col + e);
+            const float av = __ldg(a.val + e);
+            const int f0 = __ldg(a.rp + k), f1 = __ldg(a.rp + k + 1);
+            for (int f = f0 + lane; f < f1; f += 32) {
+                const int j = __ldg(a.col + f);
+                const float p = __fmul_rn(av, __ldg(a.val + f));
+                const int pos = atomicAdd(cur + (j >> bk.lw), 1);
+                stage[pos] = make_int2(j, __float_as_int(p));
+            }
+        }
+        __syncthreads();
+        // ---- each window: sums in shared memory, then the touched columns out
+        double loc = 0.0;
+        unsigned long long amax = 0;
+        int c = 0, par = 0;
+        for (int b = 0; b < NB; ++b) {
+            const int o0 = off[b], o1 = off[b + 1];
+            if (o0 == o1) continue;
+            for (int i = o0 + tid; i < o1; i += kMclThreads) {
+                const int2 ent = stage[i];
+                const int jl = ent.x & (W - 1);
+                if (atomicAdd(win + jl, (double)__int_as_float(ent.y)) == 0.0) tl[atomicAdd(s_lc + par, 1)] = jl;
+            }
+            __syncthreads();
+            const int lc = s_lc[par];
+            if (tid == 0) s_lc[par ^ 1] = 0;
+            for (int t = tid; t < lc; t += kMclThreads) {
+                const int jl = tl[t];
+                const double x = win[jl];
+                win[jl] = 0.0;
+                ex[c + t] = x;  // slots of windows already summed
+                ej[c + t] = (b << bk.lw) | jl;
+                if (square) {
+                    loc = fma(x, x, loc);
+                    const unsigned long long ax = abs_bits(x);
+                    amax = ax > amax ? ax : amax;
+                }
+            }
+            c += lc;
+            par ^= 1;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            s_lc[0] = 0;
+            s_lc[1] = 0;
+        }
+        // non-square inflation: the sum and the largest w from the list
+        double wtop = 0.0;
+        if (!square) {
+            for (int i = tid; i < c; i += kMclThreads) {
+                const double w = pow(ex[i], a.inflation);
+                loc += w;
+                wtop = fmax(wtop, w);
+            }
+        }
+        const double s = block_sum_d(loc, sh.red);
+        double wmax;
+        if (square) {
+            const double xm = __longlong_as_double(
+                (long long)block_max_u64(amax, reinterpret_cast<unsigned long long*>(sh.red)));
+            wmax = xm * xm;
+        } else {
+            wmax = block_max_d(wtop, sh.red);
+        }
+
+        // ---- candidates and the largest entry, as in k_mcl_rows
+        const bool filt = a.prune >= 0.0 && s > 0.0 && s <= 1.7e308 && wmax >= 0x1p-1000 && wmax <= 1.7e308 &&
+                          (a.prune == 0.0 || a.prune * s >= 0x1p-1000);
+        const double wlo = filt ? a.prune * s * (1.0 - 0x1p-45) : 0.0;
+        const double whi = filt ? wmax * (1.0 - 0x1p-45) : 0.0;
+        const unsigned long long xlo = filt && square ? sq_bound_bits(wlo) : 0ull;
+        const unsigned long long xhi = filt && square ? sq_bound_bits(whi) : 0ull;
+        const unsigned long long xskip = xlo < xhi ? xlo : xhi;
+        if (tid == 0) sh.cnt = 0;
+        __syncthreads();
+        double vmax = -1.0;
+        int jmax = 0x7fffffff;
+        for (int i = tid; i < c; i += kMclThreads) {
+            const double x = ex[i];
+            if (abs_bits(x) < xskip) continue;
+            const double w = square ? x * x : pow(x, a.inflation);
+            if (filt && !(w >= wlo) && !(w >= whi)) continue;
+            const int j = ej[i];
+            const double v = w / s;
+            if (v >= a.prune) {
+                const int qq = atomicAdd(&sh.cnt, 1);
+                if (qq < a.ccap) {
+                    CK[qq] = (unsigned long long)__double_as_longlong(v);
+                    CC[qq] = j;
+                }
+            }
+            if (v > vmax || (v == vmax && j < jmax)) {
+                vmax = v;
+                jmax = j;
+            }
+        }
+        __syncthreads();
+        const int nkeep = sh.cnt;
+        const int ncand = nkeep < a.ccap ? nkeep : a.ccap;
+        if (tid == 0 && nkeep > a.ccap) atomicOr(a.status, kStatusInternal);
+        {
+            double bv = vmax;
+            int bj = jmax;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (ov > bv || (ov == bv && oj < bj)) {
+                    bv = ov;
+                    bj = oj;
+                }
+            }
+            if (lane == 0) {
+                sh.red[warp] = bv;
+                sh.ired[warp] = bj;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double gv = sh.red[0];
+                int gj = sh.ired[0];
+                for (int w = 1; w < kMclThreads / 32; ++w)
+                    if (sh.red[w] > gv || (sh.red[w] == gv && sh.ired[w] < gj)) {
+                        gv = sh.red[w];
+                        gj = sh.ired[w];
+                    }
+                sh.bestj = gj;
+                sh.bestv = gv;
+            }
+            __syncthreads();
+        }
+        mcl_finish_row(a, sh, r, CK, CC, nkeep, ncand);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- heavy rows
 //
 // Rows with many products (their distinct columns a large part of n) run in
@@ -842,21 +1058,6 @@ cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// per row: its product count reaches `threshold` -> flagged and listed
-__global__ void k_mcl_heavy_mark(const int* __restrict__ rp, const int* __restrict__ col, int n, long long threshold,
-                                 unsigned char* flags, int* list, int* count) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    long long u = 0;
-    for (int e = __ldg(rp + r); e < __ldg(rp + r + 1) && u < threshold; ++e) {
-        const int k = __ldg(col + e);
-        u += __ldg(rp + k + 1) - __ldg(rp + k);
-    }
-    const bool hv = u >= threshold;
-    flags[r] = hv ? 1 : 0;
-    if (hv) list[atomicAdd(count, 1)] = r;
-}
-
 // flag := 1 if a value is not in [2^-63, FLT_MAX] (zero, negative, tiny,
 // infinite or NaN): then a product may be 0 or a sum may return to 0
 __global__ void k_mcl_check_positive(const float* __restrict__ val, long long nnz, int* flag) {
@@ -875,10 +1076,68 @@ cudaError_t launch_mcl_check_positive(const float* val, long long nnz, int* flag
     return cudaGetLastError();
 }
 
-cudaError_t launch_mcl_heavy_mark(const int* rp, const int* col, int n, long long threshold, unsigned char* flags,
-                                  int* list, int* count, cudaStream_t s) {
+// per row, by its product count u: u >= heavy -> 1 (batched path, listed in
+// hlist); bucket_lo <= u < bucket_hi and every value positive (*notpos == 0)
+// -> 2 (bucketed path, listed in blist); else 0 (per-block kernel)
+__global__ void k_mcl_mark(const int* __restrict__ rp, const int* __restrict__ col, int n, long long heavy,
+                           long long bucket_lo, long long bucket_hi, const int* notpos, unsigned char* flags,
+                           int* hlist, int* hcount, int* blist, int* bcount) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const long long stop = heavy > bucket_hi ? heavy : bucket_hi;
+    long long u = 0;
+    for (int e = __ldg(rp + r); e < __ldg(rp + r + 1) && u < stop; ++e) {
+        const int k = __ldg(col + e);
+        u += __ldg(rp + k + 1) - __ldg(rp + k);
+    }
+    unsigned char f = 0;
+    if (u >= heavy) {
+        f = 1;
+        hlist[atomicAdd(hcount, 1)] = r;
+    } else if (u >= bucket_lo && u < bucket_hi && *notpos == 0) {
+        f = 2;
+        blist[atomicAdd(bcount, 1)] = r;
+    }
+    flags[r] = f;
+}
+
+cudaError_t launch_mcl_mark(const int* rp, const int* col, int n, long long heavy, long long bucket_lo,
+                            long long bucket_hi, const int* notpos, unsigned char* flags, int* hlist, int* hcount,
+                            int* blist, int* bcount, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_mcl_heavy_mark<<<(n + 255) / 256, 256, 0, s>>>(rp, col, n, threshold, flags, list, count);
+    k_mcl_mark<<<(n + 255) / 256, 256, 0, s>>>(rp, col, n, heavy, bucket_lo, bucket_hi, notpos, flags, hlist, hcount,
+                                               blist, bcount);
+    return cudaGetLastError();
+}
+
+size_t mcl_bucket_smem(int lw, int nbk) { return 8 * ((size_t)1 << lw) + 4 * ((size_t)1 << lw) + 4 * (2 * (size_t)nbk + 1); }
+
+int mcl_bucket_blocks_per_sm(int lw, int nbk) {
+    const size_t dyn = mcl_bucket_smem(lw, nbk);
+    if (cudaFuncSetAttribute(k_mcl_rows_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mcl_rows_bucket, kMclThreads, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int blocks, cudaStream_t s) {
+    if (blocks <= 0 || b.lw < 5 || b.lw > 13) return cudaErrorInvalidValue;
+    MclBucketArgs bk;
+    bk.list = b.list;
+    bk.count = b.count;
+    bk.counter = b.counter;
+    bk.stage = b.stage;
+    bk.ej = b.ej;
+    bk.cap = b.cap;
+    bk.lw = b.lw;
+    bk.nbk = b.nbk;
+    k_mcl_rows_bucket<<<blocks, kMclThreads, mcl_bucket_smem(b.lw, b.nbk), s>>>(mcl_args(l), bk);
     return cudaGetLastError();
 }
 

@@ -214,3 +214,22 @@ def test_values_not_all_positive(tsg, handle, heavy):
     ref = {r: x for r, x in ref.items() if "v" not in x[2] or np.all(np.isfinite(x[2]["v"]))}
     assert len(ref) > M2.nrows * 0.9
     compare_rows(R.to_host(), ref)
+
+
+def test_bucketed_rows_equal_values(tsg, handle):
+    # b = 700: 490 000 products per row, inside the bucketed range (positive
+    # values, below the staging capacity) with the heavy path off; windows
+    # of 32 columns over n = 707.  prune 1e-4 keeps all 700 entries (1/700
+    # each); prune 0.01 keeps only the smallest column of the tie
+    b = 700
+    n = 7 + b
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[8:] = np.cumsum([b] * b)
+    U = gen.CSR(n, n, rp, np.tile(np.arange(7, 7 + b, dtype=np.int32), b), np.full(b * b, 1.0 / b, dtype=np.float32))
+    for prune, kept in ((1e-4, 700), (0.01, 1)):
+        R = tsg.mcl_step(tsg.DeviceCSR.from_host(U), prune=prune, topk=1000, handle=handle, heavy=-1)
+        rpo, col, val = R.to_host()
+        assert np.all(np.diff(rpo)[:7] == 0) and np.all(np.diff(rpo)[7:] == kept), prune
+        for r in (7, 300, n - 1):
+            assert col[rpo[r]:rpo[r + 1]].tolist() == list(range(7, 7 + kept)), (prune, r)
+            assert np.allclose(val[rpo[r]:rpo[r + 1]], 1.0 / kept, rtol=1e-6)
