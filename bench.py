@@ -825,6 +825,9 @@ def bench_mcl(tsg, steps):
     Mt = gen.rmat_stochastic(scale=20, edge_factor=16, seed=3)
     cur = tsg.DeviceCSR.from_host(Mt)
     h = tsg.Handle()
+    # one untimed call sizes the handle's workspaces (accumulators, staging)
+    tsg.mcl_step(cur, handle=h)
+    torch.cuda.synchronize()
     iters = []
     for it in range(3):
         rp = cur.row_ptr.cpu().numpy().astype(np.int64)
@@ -841,12 +844,16 @@ def bench_mcl(tsg, steps):
         # compulsory: the iterate read once (it is both factors), the kept
         # entries written once; streaming: 8 B (column + value) per product
         alg = csr_bytes(cur.nrows, int(rp[-1]), 4) + csr_bytes(cur.nrows, nxt.nnz, 4)
-        roof = workload_roofline(alg, ms, "k_mcl_rows (expansion fused with selection) + k_mcl_collect")
+        roof = workload_roofline(alg, ms, "k_mcl_rows / k_mcl_rows_bucket / k_mcl_heavy_* (expansion fused with "
+                                          "selection) + k_mcl_collect")
         peak = roof["peak"]
         roof["streaming_model"] = {"bytes": 8 * prods, "achieved_gbs": round(8 * prods / ms / 1e6, 1),
                                    "frac": round(8 * prods / ms / 1e6 / peak, 4)}
+        paths, ratio = h.mcl_paths()
         iters.append({"iteration": it + 1, "nnz_in": int(rp[-1]), "products": prods, "ms": round(ms, 3),
-                      "gflops": round(2 * prods / ms / 1e6, 2), "nnz_out": nxt.nnz, "roofline": roof})
+                      "gflops": round(2 * prods / ms / 1e6, 2), "nnz_out": nxt.nnz,
+                      "rows_per_path": {"per_block": paths[0], "window_summed": paths[1], "batched": paths[2]},
+                      "pilot_products_per_column": round(ratio, 2), "roofline": roof})
         cur = nxt
     h.close()
     return {"workload": "MCL on R-MAT scale 20 ef 16, f32 (f64 accumulation), 3 iterations", "iterations": iters,

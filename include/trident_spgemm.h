@@ -464,7 +464,11 @@ spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spg
  * / out->val (caller-allocated, out_nnz each; out->row_ptr from expand),
  * asynchronous.  No other call on the handle may come between the two.
  * The full expansion E is never stored: a row's kept entries (at most
- * min(products of the row, topk)) are all that is written.
+ * min(products of the row, topk)) are all that is written.  Workspace held
+ * by the handle: per block (4 per SM) n doubles, n ints and n / 32 words of
+ * accumulator, plus, for the window-summed rows, 12 bytes of staging per
+ * product of capacity (2^21) per block (about 11 GB on 152 SMs), plus the
+ * batched rows' two buffers of 48 MB.
  */
 typedef struct {
     double inflation;  /* r of the inflation step (2) */
@@ -472,12 +476,24 @@ typedef struct {
     int32_t topk;      /* keep at most this many per row (1000) */
     int32_t heavy;     /* rows with at least this many products run in batches
                           of a few rows on dense accumulators resident in L2
-                          (0: max(4096, n); < 0: never; with prune 0 never) */
+                          (0: max(4096, 2 n); < 0: never; with prune 0 never).
+                          With every value in [2^-63, FLT_MAX], rows from 4096
+                          products up to min(this, 2^21) sum their products
+                          window by window in shared memory */
+    int32_t window;    /* those rows: 0 by the pilot (spgemm_mcl_paths),
+                          1 always window-summed, -1 never */
 } spgemm_mcl_params;
 
 spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const spgemm_mcl_params* prm,
                                 int32_t* out_row_ptr, int64_t* out_nnz, spgemm_stream_t stream);
 spgemm_status spgemm_mcl_collect(spgemm_handle* h, spgemm_csr_out* out, spgemm_stream_t stream);
+/* spgemm_mcl_paths: rows of the last spgemm_mcl_expand on the handle per
+ * path -- rows[0] the per-block kernel, rows[1] window-summed in shared
+ * memory, rows[2] the L2-resident batches -- and *pilot_ratio the products
+ * per distinct column measured on up to 32 rows of the window-summed range
+ * (0 when no pilot ran; above 4 those rows were given back to the per-block
+ * kernel, whose accumulators then stay in L2).  Host only, no GPU work. */
+spgemm_status spgemm_mcl_paths(const spgemm_handle* h, int64_t* rows, double* pilot_ratio);
 
 /* ------------------------------------------------ allocation-free variant
  *

@@ -43,7 +43,7 @@ class CsrOut(ctypes.Structure):
 
 class MclParams(ctypes.Structure):
     _fields_ = [("inflation", ctypes.c_double), ("prune", ctypes.c_double), ("topk", ctypes.c_int32),
-                ("heavy", ctypes.c_int32)]
+                ("heavy", ctypes.c_int32), ("window", ctypes.c_int32)]
 
 
 class Tune(ctypes.Structure):
@@ -103,6 +103,7 @@ SIGNATURES = {
     "spgemm_csr_transpose_noalloc": ([ctypes.c_int, ctypes.POINTER(CsrIn), ctypes.POINTER(CsrOut), P], ctypes.c_int),
     "spgemm_mcl_expand": ([P, ctypes.POINTER(CsrIn), ctypes.POINTER(MclParams), P, I64P, P], ctypes.c_int),
     "spgemm_mcl_collect": ([P, ctypes.POINTER(CsrOut), P], ctypes.c_int),
+    "spgemm_mcl_paths": ([P, I64P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "spgemm_launch_count": ([P, I64P], ctypes.c_int),
     "spgemm_device_status": ([P], ctypes.c_int),
     "spgemm_set_timing": ([P, I32], ctypes.c_int),

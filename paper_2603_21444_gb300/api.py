@@ -165,6 +165,14 @@ class Handle:
     def device_status(self) -> int:
         return int(_abi.lib().spgemm_device_status(self._h))
 
+    def mcl_paths(self):
+        """Rows of the last ``mcl_step`` on this handle per path (per-block,
+        window-summed, batched) and the pilot's products per distinct column."""
+        rows = (ctypes.c_int64 * 3)()
+        ratio = ctypes.c_double()
+        check(_abi.lib().spgemm_mcl_paths(self._h, rows, ctypes.byref(ratio)), "spgemm_mcl_paths")
+        return [int(x) for x in rows], float(ratio.value)
+
     def set_timing(self, on: bool):
         check(_abi.lib().spgemm_set_timing(self._h, 1 if on else 0), "spgemm_set_timing")
 
@@ -664,14 +672,16 @@ class TridentPlan:
 # ------------------------------------------------------- Markov clustering
 
 def mcl_step(Mt: DeviceCSR, inflation: float = 2.0, prune: float = 1e-4, topk: int = 1000,
-             handle: Handle | None = None, stream=None, heavy: int = 0) -> DeviceCSR:
+             handle: Handle | None = None, stream=None, heavy: int = 0, window: int = 0) -> DeviceCSR:
     """One Markov-clustering iteration (Sec. 5.6) on the transposed
     column-stochastic matrix: expansion fused with inflation, pruning, top-k
     and renormalisation (``spgemm_mcl_expand`` / ``spgemm_mcl_collect``).
     ``heavy``: rows with at least this many products take the batched
-    dense-accumulator path (0: the library's default, < 0: never)."""
+    dense-accumulator path (0: the library's default, < 0: never);
+    ``window``: rows from 4096 products below that summed window by window in
+    shared memory -- 0 as a pilot decides, 1 always (positive values), -1 never."""
     h = handle or default_handle()
-    prm = _abi.MclParams(float(inflation), float(prune), int(topk), int(heavy))
+    prm = _abi.MclParams(float(inflation), float(prune), int(topk), int(heavy), int(window))
     dev = Mt.row_ptr.device
     rp = torch.empty(Mt.nrows + 1, dtype=torch.int32, device=dev)
     nnz = ctypes.c_int64()

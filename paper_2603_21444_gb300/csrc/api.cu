@@ -67,6 +67,8 @@ struct spgemm_handle {
     DevBuf mcl_heavy;  // ... row flags, heavy and bucket lists, two buffers of batch accumulators
     DevBuf mcl_bucket; // ... bucketed rows: staging and emitted columns per block
     long long mcl_heavy_key = -1;  // layout whose batch accumulators are known to be zero
+    double mcl_pilot_ratio = 0.0;  // products per distinct column of the last pilot (0: none ran)
+    long long mcl_paths[3] = {};   // rows of the last expand per path: per-block, window-summed, batched
     cudaStream_t mcl_side = nullptr;  // heavy-row selection, overlapping the next batch
     cudaEvent_t mcl_ev[5] = {};       // batch ready (2), buffer cleared (2), join
     DevBuf perm;    // permutation: target hits, row lengths, scan, long-row list, ranks
@@ -1469,7 +1471,8 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
                                 int32_t* out_row_ptr, int64_t* out_nnz, spgemm_stream_t stream) {
     if (!h || !csr_in_ok(Mt, true) || !prm || !out_row_ptr || !out_nnz) return SPGEMM_ERR_INVALID_ARG;
     if (Mt->nrows != Mt->ncols) return SPGEMM_ERR_SHAPE;
-    if (prm->topk < 1 || prm->topk > 1024 || !(prm->inflation > 0.0) || !(prm->prune >= 0.0))
+    if (prm->topk < 1 || prm->topk > 1024 || !(prm->inflation > 0.0) || !(prm->prune >= 0.0) || prm->window < -1 ||
+        prm->window > 1)
         return SPGEMM_ERR_INVALID_ARG;
     int dev = -1;
     TSG_CHECK(cudaGetDevice(&dev));
@@ -1477,6 +1480,8 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     note_stream(h, st);
     h->mcl_n = -1;
+    h->mcl_pilot_ratio = 0.0;
+    for (long long& x : h->mcl_paths) x = 0;
     const long long n = Mt->nrows;
     if (n == 0) {
         TSG_CHECK(cudaMemsetAsync(out_row_ptr, 0, sizeof(int), st));
@@ -1566,7 +1571,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     // < 0 turns the path off): batches of R rows whose dense accumulators
     // fit L2 together.  With prune 0 every touched column may be kept, which
     // a dense scan cannot tell from an untouched one: the path is off then.
-    const long long thr = prm->heavy > 0 ? (long long)prm->heavy : std::max<long long>(4096, n);
+    const long long thr = prm->heavy > 0 ? (long long)prm->heavy : std::max<long long>(4096, 2 * n);
     const long long acc_row = 8 * stride;
     const bool heavy_on = prm->heavy >= 0 && prm->prune > 0.0 && acc_row <= (64ll << 20);
     int H = 0;
@@ -1578,7 +1583,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     const size_t o_bck = o_sc + align16((size_t)R * (8 + 8 + 4 + 4 + 4));
     const size_t o_bcc = o_bck + 8 * (size_t)R * ccap;
     const size_t buf_bytes = align16(o_bcc + 4 * (size_t)R * ccap + 4 * (size_t)R * kMclMaxList);
-    const size_t o_buf = o_hc + 16;
+    const size_t o_buf = o_hc + 32;  // the 16 bytes after the counters: the pilot's totals
     const size_t heavy_bytes = heavy_on ? o_buf + 2 * buf_bytes : o_buf;
     if (h->mcl_heavy.n < heavy_bytes) {
         TSG_TRY(grow(h, h->mcl_heavy, heavy_bytes));
@@ -1591,16 +1596,17 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     // a column's first add finds 0 (no bitmap), and the bucketed path applies
     TSG_CHECK(launch_mcl_check_positive(static_cast<const float*>(Mt->val), Mt->nnz, ctr4 + 1, h->sms, st));
     ++h->launches;
-    // 2c. bucketed mid rows (4096 <= products < the staging capacity 2^20,
-    // below the heavy threshold): windows of 2^lw columns, at most 64 per
-    // row up to n = 2^18 and 4096 columns wide beyond
+    // 2c. bucketed mid rows (4096 <= products < the staging capacity 2^21,
+    // below the heavy threshold; 12 bytes of staging per product and block):
+    // windows of 2^lw columns, at most 64 per row up to n = 2^18 and 4096
+    // columns wide beyond
     int lw = 5;
     while (lw < 12 && (n >> lw) > 64) ++lw;
     const int nbk = (int)((n + (1ll << lw) - 1) >> lw);
     const int bps = nbk <= 2048 ? mcl_bucket_blocks_per_sm(lw, nbk) : 0;
     const int bblocks = (int)std::min<long long>(slots, (long long)h->sms * std::min(bps, 4));
-    const long long bcap = heavy_on ? std::min<long long>(1ll << 20, thr) : (1ll << 20);
-    const long long blo = bblocks > 0 ? 4096 : (1ll << 62);
+    const long long bcap = heavy_on ? std::min<long long>(1ll << 21, thr) : (1ll << 21);
+    const long long blo = bblocks > 0 && prm->window >= 0 ? 4096 : (1ll << 62);
     if (heavy_on) {
         const long long hkey = (long long)stride * 4096 * 32 + (long long)R * 4096 + (ccap & 4095);
         if (h->mcl_heavy_key != hkey) {
@@ -1616,9 +1622,34 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     TSG_CHECK(cudaStreamSynchronize(st));
     const int* got = reinterpret_cast<const int*>(p_ll + 2);
     H = got[0];
-    const int NBR = got[2];
+    int NBR = got[2];
     ml.positive = got[1] == 0 ? 1 : 0;
     ml.heavy = H + NBR > 0 ? reinterpret_cast<const unsigned char*>(hv) : nullptr;
+    ml.skip = 3;
+    if (NBR > 0 && prm->window == 0) {
+        // pilot: products per distinct column over up to 32 evenly spaced
+        // rows of the window-summed range; above 4 (a clustered iterate,
+        // whose many adds to few columns serialise in shared memory while
+        // its small accumulator footprint stays in L2 for the per-block
+        // kernel) those rows go back to the per-block kernel
+        const int ns = std::min(32, NBR);
+        unsigned long long* tot = reinterpret_cast<unsigned long long*>(hv + o_hc + 16);
+        TSG_CHECK(cudaMemsetAsync(tot, 0, 16, st));
+        TSG_CHECK(launch_mcl_pilot(ml, reinterpret_cast<const int*>(hv + o_bl), ns, NBR / ns, tot, st));
+        ++h->launches;
+        TSG_CHECK(readback(h, p_ll + 4, tot, 16, st));
+        TSG_CHECK(cudaStreamSynchronize(st));
+        const unsigned long long pp = reinterpret_cast<const unsigned long long*>(p_ll + 4)[0];
+        const unsigned long long pd = reinterpret_cast<const unsigned long long*>(p_ll + 4)[1];
+        h->mcl_pilot_ratio = pd ? (double)pp / (double)pd : 0.0;
+        if (pd == 0 || pp > 4 * pd) {
+            ml.skip = 1;
+            NBR = 0;
+        }
+    }
+    h->mcl_paths[2] = H;
+    h->mcl_paths[1] = NBR;
+    h->mcl_paths[0] = n - H - NBR;
     TSG_CHECK(launch_mcl_rows(ml, slots, st));
     if (NBR > 0) {
         const size_t sbytes = (size_t)bblocks * bcap * 8, ebytes = (size_t)bblocks * bcap * 4;
@@ -1684,6 +1715,13 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     *out_nnz = p_ll[0];
     h->mcl_n = (int)n;
     h->mcl_total = total;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_mcl_paths(const spgemm_handle* h, int64_t* rows, double* pilot_ratio) {
+    if (!h || !rows || !pilot_ratio) return SPGEMM_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i) rows[i] = h->mcl_paths[i];
+    *pilot_ratio = h->mcl_pilot_ratio;
     return SPGEMM_OK;
 }
 

@@ -132,7 +132,8 @@ struct MclLaunch {
     double prune;
     int topk;
     unsigned* status;
-    const unsigned char* heavy = nullptr;  // rows left to the batched path
+    const unsigned char* heavy = nullptr;  // row flags: 1 batched, 2 window-summed
+    int skip = 0;                          // flag bits whose rows k_mcl_rows leaves
     int positive = 0;                      // every value in [2^-63, FLT_MAX]
 };
 // batched heavy rows: at most kMclBatch rows per batch, each with a dense
@@ -167,6 +168,8 @@ struct MclBucketLaunch {
     int lw;
     int nbk;
 };
+cudaError_t launch_mcl_pilot(const MclLaunch& l, const int* rows, int nrows, int step, unsigned long long* tot,
+                             cudaStream_t s);
 size_t mcl_bucket_smem(int lw, int nbk);
 int mcl_bucket_blocks_per_sm(int lw, int nbk);
 cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int blocks, cudaStream_t s);

@@ -138,7 +138,8 @@ struct MclArgs {
     double prune;
     int topk;
     unsigned* status;
-    const unsigned char* heavy;  // nonzero: the row is left to the batched path
+    const unsigned char* heavy;  // row flags: 1 batched path, 2 window-summed path
+    int skip;                    // flags (bits) whose rows this kernel leaves
     int positive;                // every value is positive and no product underflows to 0
 };
 
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
         __syncthreads();
         const int r = sh.row;
         if (r >= a.n) break;
-        if (a.heavy && a.heavy[r]) {
+        if (a.heavy && (a.heavy[r] & a.skip)) {
             __syncthreads();  // every thread has read the row before the next is drawn
             continue;
         }
@@ -709,6 +710,49 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclB
     }
 }
 
+// Pilot of the window-summed path: block b expands row rows[b * step] into
+// its private accumulator (positive values: the add that finds 0 counts a
+// distinct column), adds the row's products and distinct columns to tot[0]
+// and tot[1], and clears what it touched.  Rows whose products pile onto
+// few columns (a clustered iterate) are summed faster by k_mcl_rows, whose
+// accumulator footprint is then small and stays in L2.
+__global__ void __launch_bounds__(kMclThreads) k_mcl_pilot(MclArgs a, const int* rows, int step,
+                                                           unsigned long long* tot) {
+    __shared__ int cnt;
+    __shared__ unsigned long long prods;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* D = a.dense + (long long)blockIdx.x * a.stride;
+    int* L = a.touched + (long long)blockIdx.x * a.stride;
+    const int r = rows[(long long)blockIdx.x * step];
+    if (tid == 0) {
+        cnt = 0;
+        prods = 0;
+    }
+    __syncthreads();
+    const int e0 = __ldg(a.rp + r), e1 = __ldg(a.rp + r + 1);
+    unsigned long long u = 0;
+    for (int e = e0 + warp; e < e1; e += kMclThreads / 32) {
+        const int k = __ldg(a.col + e);
+        const float av = __ldg(a.val + e);
+        const int f0 = __ldg(a.rp + k), f1 = __ldg(a.rp + k + 1);
+        if (lane == 0) u += f1 - f0;
+        for (int f = f0 + lane; f < f1; f += 32) {
+            const int j = __ldg(a.col + f);
+            if (atomicAdd(D + j, (double)__fmul_rn(av, __ldg(a.val + f))) == 0.0) L[atomicAdd(&cnt, 1)] = j;
+        }
+    }
+    if (lane == 0) atomicAdd(&prods, u);
+    __threadfence();
+    __syncthreads();
+    const int c = cnt;
+    for (int i = tid; i < c; i += kMclThreads) __stcg(D + L[i], 0.0);
+    if (tid == 0) {
+        atomicAdd(tot, prods);
+        atomicAdd(tot + 1, (unsigned long long)c);
+    }
+}
+
+
 // ---------------------------------------------------------------- heavy rows
 //
 // Rows with many products (their distinct columns a large part of n) run in
@@ -1031,6 +1075,7 @@ MclArgs mcl_args(const MclLaunch& l) {
     a.topk = l.topk;
     a.status = l.status;
     a.heavy = l.heavy;
+    a.skip = l.skip;
     a.positive = l.positive;
     return a;
 }
@@ -1052,6 +1097,13 @@ MclHeavyArgs heavy_args(const MclLaunch& l, const MclHeavyLaunch& hb) {
     return h;
 }
 }  // namespace
+
+cudaError_t launch_mcl_pilot(const MclLaunch& l, const int* rows, int nrows, int step, unsigned long long* tot,
+                             cudaStream_t s) {
+    if (nrows <= 0 || step <= 0) return cudaErrorInvalidValue;
+    k_mcl_pilot<<<nrows, kMclThreads, 0, s>>>(mcl_args(l), rows, step, tot);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s) {
     k_mcl_rows<<<blocks, kMclThreads, 0, s>>>(mcl_args(l));

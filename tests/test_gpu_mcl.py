@@ -216,20 +216,48 @@ def test_values_not_all_positive(tsg, handle, heavy):
     compare_rows(R.to_host(), ref)
 
 
-def test_bucketed_rows_equal_values(tsg, handle):
-    # b = 700: 490 000 products per row, inside the bucketed range (positive
-    # values, below the staging capacity) with the heavy path off; windows
-    # of 32 columns over n = 707.  prune 1e-4 keeps all 700 entries (1/700
-    # each); prune 0.01 keeps only the smallest column of the tie
+def test_clustered_rows_equal_values(tsg, handle):
+    # b = 700: 490 000 products per row onto 700 columns, in the
+    # window-summed range with the heavy path off; the pilot measures 700
+    # products per distinct column and gives the rows back to the per-block
+    # kernel; forced onto the window-summed path (every add of a window on
+    # the same 700 words) and kept off it, the results are the same.  prune 1e-4 keeps all 700 entries (1/700 each); prune 0.01
+    # keeps only the smallest column of the tie
     b = 700
     n = 7 + b
     rp = np.zeros(n + 1, dtype=np.int64)
     rp[8:] = np.cumsum([b] * b)
     U = gen.CSR(n, n, rp, np.tile(np.arange(7, 7 + b, dtype=np.int32), b), np.full(b * b, 1.0 / b, dtype=np.float32))
     for prune, kept in ((1e-4, 700), (0.01, 1)):
-        R = tsg.mcl_step(tsg.DeviceCSR.from_host(U), prune=prune, topk=1000, handle=handle, heavy=-1)
-        rpo, col, val = R.to_host()
-        assert np.all(np.diff(rpo)[:7] == 0) and np.all(np.diff(rpo)[7:] == kept), prune
-        for r in (7, 300, n - 1):
-            assert col[rpo[r]:rpo[r + 1]].tolist() == list(range(7, 7 + kept)), (prune, r)
-            assert np.allclose(val[rpo[r]:rpo[r + 1]], 1.0 / kept, rtol=1e-6)
+        for window in (0, 1, -1):
+            R = tsg.mcl_step(tsg.DeviceCSR.from_host(U), prune=prune, topk=1000, handle=handle, heavy=-1,
+                             window=window)
+            paths, ratio = handle.mcl_paths()
+            want = {0: ([n, 0, 0], 700.0), 1: ([7, b, 0], 0.0), -1: ([n, 0, 0], 0.0)}[window]
+            assert (paths, ratio) == want, (window, paths, ratio)
+            rpo, col, val = R.to_host()
+            assert np.all(np.diff(rpo)[:7] == 0) and np.all(np.diff(rpo)[7:] == kept), (prune, window)
+            for r in (7, 300, n - 1):
+                assert col[rpo[r]:rpo[r + 1]].tolist() == list(range(7, 7 + kept)), (prune, window, r)
+                assert np.allclose(val[rpo[r]:rpo[r + 1]], 1.0 / kept, rtol=1e-6)
+
+
+@pytest.mark.parametrize("heavy", [-1, 0])
+def test_window_summed_rows_rmat_scale16(tsg, handle, heavy):
+    # the rows from 4096 products on the window-summed path (forced; windows
+    # of 1024 columns); heavy 0 also sends the rows from 2^18 products to the
+    # batches.  Sampled rows: up to 1500 of the window-summed range plus 1500
+    # others
+    Mt = gen.rmat_stochastic(scale=16, edge_factor=16, seed=23)
+    R = tsg.mcl_step(tsg.DeviceCSR.from_host(Mt), handle=handle, heavy=heavy if heavy else 1 << 18, window=1)
+    torch.cuda.synchronize()
+    paths, ratio = handle.mcl_paths()
+    assert paths[1] > 0 and ratio == 0.0, (paths, ratio)
+    if heavy == 0:
+        assert paths[2] > 0, paths
+    u = oracle.row_products(Mt, Mt)
+    mid = np.nonzero((u >= 4096) & (u < (1 << 18)))[0]
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([rng.choice(mid, min(1500, mid.size), replace=False),
+                                     rng.choice(Mt.nrows, 1500, replace=False)]))
+    compare_rows(R.to_host(), oracle.mcl_step(Mt, rows=rows))
