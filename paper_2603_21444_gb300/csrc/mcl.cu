@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclB
     __shared__ int s_row, s_lc[2];
     const int W = 1 << bk.lw, NB = bk.nbk;
     double* win = reinterpret_cast<double*>(dyn);
-    int* tl = reinterpret_cast<int*>(dyn + 8 * (size_t)W);
-    int* off = tl + W;     // NB + 1
+    unsigned short* tl = reinterpret_cast<unsigned short*>(dyn + 8 * (size_t)W);  // window-local columns
+    int* off = reinterpret_cast<int*>(dyn + 10 * (size_t)W);                     // NB + 1
     int* cur = off + NB + 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int2* stage = bk.stage + (long long)blockIdx.x * bk.cap;
@@ -596,7 +596,8 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclB
             for (int i = o0 + tid; i < o1; i += kMclThreads) {
                 const int2 ent = stage[i];
                 const int jl = ent.x & (W - 1);
-                if (atomicAdd(win + jl, (double)__int_as_float(ent.y)) == 0.0) tl[atomicAdd(s_lc + par, 1)] = jl;
+                if (atomicAdd(win + jl, (double)__int_as_float(ent.y)) == 0.0)
+                    tl[atomicAdd(s_lc + par, 1)] = (unsigned short)jl;
             }
             __syncthreads();
             const int lc = s_lc[par];
@@ -1162,7 +1163,7 @@ cudaError_t launch_mcl_mark(const int* rp, const int* col, int n, long long heav
     return cudaGetLastError();
 }
 
-size_t mcl_bucket_smem(int lw, int nbk) { return 8 * ((size_t)1 << lw) + 4 * ((size_t)1 << lw) + 4 * (2 * (size_t)nbk + 1); }
+size_t mcl_bucket_smem(int lw, int nbk) { return 10 * ((size_t)1 << lw) + 4 * (2 * (size_t)nbk + 1); }
 
 int mcl_bucket_blocks_per_sm(int lw, int nbk) {
     const size_t dyn = mcl_bucket_smem(lw, nbk);
