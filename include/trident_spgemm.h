@@ -466,9 +466,10 @@ spgemm_status spgemm_csr_permute(spgemm_handle* h, spgemm_dtype dtype, const spg
  * The full expansion E is never stored: a row's kept entries (at most
  * min(products of the row, topk)) are all that is written.  Workspace held
  * by the handle: per block (4 per SM) n doubles, n ints and n / 32 words of
- * accumulator, plus, for the window-summed rows, 12 bytes of staging per
- * product of capacity (2^21) per block (about 11 GB on 152 SMs), plus the
- * batched rows' two buffers of 48 MB.
+ * accumulator, plus, for the window-summed rows (up to 6 blocks per SM, 5
+ * with 4096-column windows), 12 bytes of staging per product of capacity
+ * (2^21) per block (about 19 GB on 152 SMs), plus the batched rows' two
+ * buffers of 48 MB.
  */
 typedef struct {
     double inflation;  /* r of the inflation step (2) */

@@ -1528,9 +1528,12 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
         ccap = std::max<long long>(4096, (long long)std::ceil(2.0 / prm->prune));
     ccap = std::min(ccap, stride);
     const size_t o_bm = 12 * (size_t)stride * slots;
+    // candidate lists for the per-block kernel's blocks and for up to six
+    // blocks per SM of the window-summed kernel
+    const int cslots = (int)std::max<long long>(slots, std::min<long long>(n, (long long)h->sms * 6));
     const size_t o_ck = align16(o_bm + 4 * (size_t)bm_words * slots);
-    const size_t o_cc = o_ck + 8 * (size_t)ccap * slots;
-    const size_t acc_bytes = o_cc + 4 * (size_t)ccap * slots;
+    const size_t o_cc = o_ck + 8 * (size_t)ccap * cslots;
+    const size_t acc_bytes = o_cc + 4 * (size_t)ccap * cslots;
     if (h->mcl_acc.n < acc_bytes) {
         TSG_TRY(grow(h, h->mcl_acc, acc_bytes));
         h->mcl_acc_key = -1;
@@ -1604,7 +1607,7 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
     while (lw < 12 && (n >> lw) > 64) ++lw;
     const int nbk = (int)((n + (1ll << lw) - 1) >> lw);
     const int bps = nbk <= 2048 ? mcl_bucket_blocks_per_sm(lw, nbk) : 0;
-    const int bblocks = (int)std::min<long long>(slots, (long long)h->sms * std::min(bps, 4));
+    const int bblocks = (int)std::min<long long>(cslots, (long long)h->sms * std::min(bps, 6));
     const long long bcap = heavy_on ? std::min<long long>(1ll << 21, thr) : (1ll << 21);
     const long long blo = bblocks > 0 && prm->window >= 0 ? 4096 : (1ll << 62);
     if (heavy_on) {

@@ -152,16 +152,14 @@ struct MclShared {
     double red[32];
     int ired[32];
     unsigned hist[256];
-    int kcol[kMclMaxK];
-    float kval[kMclMaxK];
 };
 
 // Keep rule, renormalisation and output of row r from its candidates (the
 // entries with v >= prune: CK their values' bits, CC their columns; nkeep of
 // them found, the first ncand stored) and, when none reached the prune, the
 // largest entry sh.bestj / sh.bestv.  Called by every thread of the block.
-__device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const unsigned long long* CK, const int* CC,
-                               int nkeep, int ncand) {
+__device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int* kcol, float* kval, int r,
+                               const unsigned long long* CK, const int* CC, int nkeep, int ncand) {
     const int tid = threadIdx.x;
     // ---- the keep rule: mode 0 prune only, 1 largest only, 2 top-k
     const int mode = nkeep == 0 ? 1 : (nkeep > a.topk ? 2 : 0);
@@ -252,8 +250,8 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
     __syncthreads();
     if (mode == 1) {
         if (tid == 0 && bestj != 0x7fffffff) {
-            sh.kcol[0] = bestj;
-            sh.kval[0] = (float)(sh.bestv / t);
+            kcol[0] = bestj;
+            kval[0] = (float)(sh.bestv / t);
             sh.cnt = 1;
         }
     } else {
@@ -261,8 +259,8 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
             if (!kept_q(q)) continue;
             const int o = atomicAdd(&sh.cnt, 1);
             if (o < kMclMaxK) {
-                sh.kcol[o] = CC[q];
-                sh.kval[o] = (float)(__longlong_as_double((long long)CK[q]) / t);
+                kcol[o] = CC[q];
+                kval[o] = (float)(__longlong_as_double((long long)CK[q]) / t);
             }
         }
     }
@@ -276,7 +274,7 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
         // bitonic sort of the kept entries by column (padding sorts last)
         int P = 1;
         while (P < nout) P <<= 1;
-        for (int i = nout + tid; i < P; i += kMclThreads) sh.kcol[i] = 0x7fffffff;
+        for (int i = nout + tid; i < P; i += kMclThreads) kcol[i] = 0x7fffffff;
         __syncthreads();
         for (int size = 2; size <= P; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -284,13 +282,13 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
                     const int pj = i ^ stride;
                     if (pj > i) {
                         const bool up = (i & size) == 0;
-                        const int ci = sh.kcol[i], cj = sh.kcol[pj];
+                        const int ci = kcol[i], cj = kcol[pj];
                         if ((ci > cj) == up) {
-                            sh.kcol[i] = cj;
-                            sh.kcol[pj] = ci;
-                            const float t2 = sh.kval[i];
-                            sh.kval[i] = sh.kval[pj];
-                            sh.kval[pj] = t2;
+                            kcol[i] = cj;
+                            kcol[pj] = ci;
+                            const float t2 = kval[i];
+                            kval[i] = kval[pj];
+                            kval[pj] = t2;
                         }
                     }
                 }
@@ -298,8 +296,8 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
             }
         }
         for (int q = tid; q < nout; q += kMclThreads) {
-            a.tmp_col[slot + q] = sh.kcol[q];
-            a.tmp_val[slot + q] = sh.kval[q];
+            a.tmp_col[slot + q] = kcol[q];
+            a.tmp_val[slot + q] = kval[q];
         }
         if (tid == 0) a.kept[r] = nout;
     }
@@ -307,6 +305,8 @@ __device__ void mcl_finish_row(const MclArgs& a, MclShared& sh, int r, const uns
 
 __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
     __shared__ MclShared sh;
+    __shared__ int kcol[kMclMaxK];
+    __shared__ float kval[kMclMaxK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* D = a.dense + (long long)blockIdx.x * a.stride;
     unsigned* BM = a.bitmap + (long long)blockIdx.x * a.bm_words;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
             __syncthreads();
         }
 
-        mcl_finish_row(a, sh, r, CK, CC, nkeep, ncand);
+        mcl_finish_row(a, sh, kcol, kval, r, CK, CC, nkeep, ncand);
         // ---- clear the accumulator and the bitmap for the next row (a pass
         // of its own: a store right behind the load of the same word in the
         // candidate pass held every iteration for the load's round trip)
@@ -506,6 +506,11 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows(MclArgs a) {
 // is a stream, where the per-block kernel's random adds into an 8 MB
 // accumulator miss L2.
 
+__host__ __device__ inline size_t mcl_window_bytes(int lw) {
+    const size_t b = 8 * ((size_t)1 << lw);
+    return b > 8 * (size_t)kMclMaxK ? b : 8 * (size_t)kMclMaxK;
+}
+
 struct MclBucketArgs {
     const int* list;     // the rows of this path
     int count;           // how many
@@ -522,9 +527,12 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclB
     __shared__ MclShared sh;
     __shared__ int s_row, s_lc[2];
     const int W = 1 << bk.lw, NB = bk.nbk;
+    // window sums (at least 8 KB: the row's kept entries are gathered there
+    // at the end) | window-local touched columns | window offsets, cursors
+    const size_t wb = mcl_window_bytes(bk.lw);
     double* win = reinterpret_cast<double*>(dyn);
-    unsigned short* tl = reinterpret_cast<unsigned short*>(dyn + 8 * (size_t)W);  // window-local columns
-    int* off = reinterpret_cast<int*>(dyn + 10 * (size_t)W);                     // NB + 1
+    unsigned short* tl = reinterpret_cast<unsigned short*>(dyn + wb);
+    int* off = reinterpret_cast<int*>(dyn + wb + 2 * (size_t)W);  // NB + 1
     int* cur = off + NB + 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int2* stage = bk.stage + (long long)blockIdx.x * bk.cap;
@@ -706,7 +714,12 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_rows_bucket(MclArgs a, MclB
             }
             __syncthreads();
         }
-        mcl_finish_row(a, sh, r, CK, CC, nkeep, ncand);
+        // the kept entries are gathered in the window buffer (the windows
+        // are done), which is zero again before the next row
+        mcl_finish_row(a, sh, reinterpret_cast<int*>(win), reinterpret_cast<float*>(win) + kMclMaxK, r, CK, CC,
+                       nkeep, ncand);
+        __syncthreads();
+        for (int i = tid; i < kMclMaxK; i += kMclThreads) win[i] = 0.0;
         __syncthreads();
     }
 }
@@ -965,6 +978,8 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_heavy_cand(MclHeavyArgs h) 
 // then the keep rule and the output as in k_mcl_rows.
 __global__ void __launch_bounds__(kMclThreads) k_mcl_heavy_select(MclHeavyArgs h) {
     __shared__ MclShared sh;
+    __shared__ int kcol[kMclMaxK];
+    __shared__ float kval[kMclMaxK];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MclArgs& a = h.a;
     const int r = h.rows[b];
@@ -1017,7 +1032,7 @@ __global__ void __launch_bounds__(kMclThreads) k_mcl_heavy_select(MclHeavyArgs h
         }
         __syncthreads();
     }
-    mcl_finish_row(a, sh, r, h.ck + (long long)b * a.ccap, h.cc + (long long)b * a.ccap, nkeep, ncand);
+    mcl_finish_row(a, sh, kcol, kval, r, h.ck + (long long)b * a.ccap, h.cc + (long long)b * a.ccap, nkeep, ncand);
 }
 
 __global__ void k_mcl_bounds(const int* __restrict__ rp, const int* __restrict__ col, int n, int topk, int* ub) {
@@ -1163,7 +1178,9 @@ cudaError_t launch_mcl_mark(const int* rp, const int* col, int n, long long heav
     return cudaGetLastError();
 }
 
-size_t mcl_bucket_smem(int lw, int nbk) { return 10 * ((size_t)1 << lw) + 4 * (2 * (size_t)nbk + 1); }
+size_t mcl_bucket_smem(int lw, int nbk) {
+    return mcl_window_bytes(lw) + 2 * ((size_t)1 << lw) + 4 * (2 * (size_t)nbk + 1);
+}
 
 int mcl_bucket_blocks_per_sm(int lw, int nbk) {
     const size_t dyn = mcl_bucket_smem(lw, nbk);
