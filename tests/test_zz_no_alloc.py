@@ -5,7 +5,8 @@ point.
 
 This file is collected last so that, if it fails, a run stopping at the first
 failure has already run every other test; it also passes alone in a fresh
-process."""
+process.  The entry point is also captured into a CUDA graph and replayed
+on new values."""
 import ctypes
 
 import numpy as np
@@ -84,3 +85,33 @@ def test_noalloc_rejects_oversize_request(lib):
                       torch.empty(0, dtype=torch.float64, device="cuda"))
     rc, _ = _noalloc_transpose(lib, X, torch.float64)
     assert rc == 11  # SPGEMM_ERR_UNSUPPORTED
+
+
+def test_noalloc_under_graph_capture(lib):
+    # after one call outside capture (it looks up the array's address), the
+    # entry point is captured into a CUDA graph in the global error mode, in
+    # which any device allocation or synchronising call from any thread
+    # during the capture fails it; replayed after new values are written
+    # into X, the graph gives the allocating transpose's bits
+    import paper_2603_21444_gb300 as tsg
+    from paper_2603_21444_gb300 import _abi
+    from paper_2603_21444_gb300 import autograd as ag
+    X = tsg.DeviceCSR.from_host(gen.er_variable(2500, 1800, 20, 9, np.float64, "normal", p_empty=0.1))
+    rc, T = _noalloc_transpose(lib, X, torch.float64)
+    assert rc == 0
+    torch.cuda.synchronize()
+    xin, tout = X.as_in(), T.as_out()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        rc = lib.spgemm_csr_transpose_noalloc(_abi.F64, ctypes.byref(xin), ctypes.byref(tout),
+                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    X.val.copy_(torch.randn(X.val.numel(), dtype=torch.float64, device=X.val.device))
+    T.col.zero_()
+    T.val.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    R = ag.transpose(X)
+    torch.cuda.synchronize()
+    for a, b in zip(T.to_host(), R.to_host()):
+        assert np.array_equal(a, b)
