@@ -1691,9 +1691,13 @@ spgemm_status spgemm_mcl_expand(spgemm_handle* h, const spgemm_csr_in* Mt, const
             hb.mlist = reinterpret_cast<int*>(bb + o_bcc + 4 * (size_t)R * ccap);
             // the buffer's previous batch must be selected and cleared
             if (bi >= 2) TSG_CHECK(cudaStreamWaitEvent(st, h->mcl_ev[2 + q], 0));
+            // expansion on the caller's stream; the dense scans, the
+            // selection and the clear on the second one, overlapping the
+            // next batch's expansion into the other buffer
             TSG_CHECK(launch_mcl_heavy_batch(ml, hb, h->sms, st));
             TSG_CHECK(cudaEventRecord(h->mcl_ev[q], st));
             TSG_CHECK(cudaStreamWaitEvent(h->mcl_side, h->mcl_ev[q], 0));
+            TSG_CHECK(launch_mcl_heavy_scans(ml, hb, h->sms, h->mcl_side));
             TSG_CHECK(launch_mcl_heavy_select(ml, hb, h->mcl_side));
             TSG_CHECK(cudaMemsetAsync(bb, 0, o_bck, h->mcl_side));
             TSG_CHECK(cudaEventRecord(h->mcl_ev[2 + q], h->mcl_side));

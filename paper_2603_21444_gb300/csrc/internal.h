@@ -174,6 +174,7 @@ size_t mcl_bucket_smem(int lw, int nbk);
 int mcl_bucket_blocks_per_sm(int lw, int nbk);
 cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int blocks, cudaStream_t s);
 cudaError_t launch_mcl_heavy_batch(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s);
+cudaError_t launch_mcl_heavy_scans(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s);
 cudaError_t launch_mcl_heavy_select(const MclLaunch& l, const MclHeavyLaunch& hb, cudaStream_t s);
 cudaError_t launch_mcl_bounds(const int* rp, const int* col, int n, int topk, int* ub, cudaStream_t s);
 cudaError_t launch_mcl_rows(const MclLaunch& l, int blocks, cudaStream_t s);

@@ -1213,9 +1213,14 @@ cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int 
 
 cudaError_t launch_mcl_heavy_batch(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s) {
     if (hb.nb <= 0 || hb.nb > kMclBatch) return cudaErrorInvalidValue;
+    // three blocks per SM: room is left for the previous batch's scans and selection
+    k_mcl_heavy_expand<<<sms * 3, kMclThreads, 0, s>>>(heavy_args(l, hb));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mcl_heavy_scans(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s) {
+    if (hb.nb <= 0 || hb.nb > kMclBatch) return cudaErrorInvalidValue;
     const MclHeavyArgs h = heavy_args(l, hb);
-    // three blocks per SM: room is left for the previous batch's selection
-    k_mcl_heavy_expand<<<sms * 3, kMclThreads, 0, s>>>(h);
     const long long tiles = (l.stride / 8 + kMclThreads - 1) / kMclThreads;  // chunks of 8 per thread
     const int gx = (int)std::max<long long>(1, std::min<long long>(tiles, (8ll * sms + hb.nb - 1) / hb.nb));
     k_mcl_heavy_sums<<<dim3(gx, hb.nb), kMclThreads, 0, s>>>(h);
