@@ -1213,8 +1213,9 @@ cudaError_t launch_mcl_bucket(const MclLaunch& l, const MclBucketLaunch& b, int 
 
 cudaError_t launch_mcl_heavy_batch(const MclLaunch& l, const MclHeavyLaunch& hb, int sms, cudaStream_t s) {
     if (hb.nb <= 0 || hb.nb > kMclBatch) return cudaErrorInvalidValue;
-    // three blocks per SM: room is left for the previous batch's scans and selection
-    k_mcl_heavy_expand<<<sms * 3, kMclThreads, 0, s>>>(heavy_args(l, hb));
+    // six blocks per SM (30 registers, 8 fit): room is left for the previous
+    // batch's scans and selection on the other stream
+    k_mcl_heavy_expand<<<sms * 6, kMclThreads, 0, s>>>(heavy_args(l, hb));
     return cudaGetLastError();
 }
 
